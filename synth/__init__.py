@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module draws random numbers and formats data; it holds none of the
+reconciliation or decoding arithmetic (no octonion products, no syndromes,
+no LLRs). Both the CUDA path and the CPU oracle consume what it returns.
+
+Workload recipe (stand-in for the paper's codes, which are not published):
+
+* ``protograph_code``: a QC multi-edge base matrix of ``mb`` rows and
+  ``nb = mb + 1`` columns. The ``n_heavy`` leftmost columns are heavy: each
+  gets one circulant in every row plus, in ``extra[j]`` rows drawn without
+  replacement, a second circulant with a different shift (``per_row`` > 1
+  gives every row that many circulants instead). The remaining columns are
+  degree-1 identity blocks on rows 0, 1, ... (shift 0), forming the long
+  unshifted diagonal of Sec. III-D. Shifts are uniform in [0, Z).
+* ``channel_frame``: x ~ N(0,1), z ~ N(0, 1/snr), y = x + z (the virtual
+  BIAWGN channel of Sec. II-C) and Bob's uniform bits.
+
+Generator: numpy PCG64. Code seed 1; frame f uses seed 1000 + f.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CODE_SEED = 1
+FRAME_SEED0 = 1000
+
+
+def protograph_code(mb: int = 49, Z: int = 512, n_heavy: int = 2,
+                    extra=(11, 10), per_row: int = 1,
+                    seed: int = CODE_SEED) -> dict:
+    """Circulant list of the seeded multi-edge protograph code.
+
+    Returns a dict with ``mb, nb, Z`` and int32 arrays ``row, col, shift``
+    (one entry per circulant, sorted by row, then column).
+    """
+    nb = mb + 1
+    n_deg1 = nb - n_heavy
+    if n_deg1 > mb:
+        raise ValueError("more degree-1 columns than rows")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    entries = []  # (row, col, shift)
+    for j in range(n_heavy):
+        mult = np.full(mb, per_row, dtype=np.int64)
+        if per_row == 1 and extra is not None and j < len(extra) and extra[j] > 0:
+            rows2 = rng.choice(mb, size=int(extra[j]), replace=False)
+            mult[rows2] += 1
+        for r in range(mb):
+            k = int(mult[r])
+            if k > Z:
+                raise ValueError("more circulants in one entry than shifts")
+            shifts = rng.choice(Z, size=k, replace=False)
+            for s in shifts:
+                entries.append((r, j, int(s)))
+    for d in range(n_deg1):
+        entries.append((d, n_heavy + d, 0))
+    entries.sort(key=lambda e: (e[0], e[1]))
+    arr = np.array(entries, dtype=np.int64).reshape(-1, 3)
+    return {
+        "mb": mb, "nb": nb, "Z": Z,
+        "row": arr[:, 0].astype(np.int32),
+        "col": arr[:, 1].astype(np.int32),
+        "shift": arr[:, 2].astype(np.int32),
+    }
+
+
+def rate002_code(Z: int, seed: int = CODE_SEED) -> dict:
+    """Rate 0.02: 49x50 base, two heavy columns of degree 60 and 59."""
+    return protograph_code(49, Z, n_heavy=2, extra=(11, 10), seed=seed)
+
+
+def rate005_code(Z: int, seed: int = CODE_SEED) -> dict:
+    """Rate 0.05: 19x20 base, one heavy column with two circulants per row."""
+    return protograph_code(19, Z, n_heavy=1, extra=None, per_row=2, seed=seed)
+
+
+def rate010_code(Z: int, seed: int = CODE_SEED) -> dict:
+    """Rate 0.10: 9x10 base, one heavy column with two circulants per row."""
+    return protograph_code(9, Z, n_heavy=1, extra=None, per_row=2, seed=seed)
+
+
+def channel_frame(n: int, snr: float, seed: int):
+    """One frame of the virtual BIAWGN channel.
+
+    Returns float64 ``x`` (Alice), ``y = x + z`` (Bob), and uint8 ``bits``
+    (Bob's uniform codeword-position bits; in syndrome form they need not
+    be a codeword).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.standard_normal(n)
+    z = rng.standard_normal(n) * np.sqrt(1.0 / snr)
+    bits = rng.integers(0, 2, size=n, dtype=np.uint8)
+    return x, x + z, bits
+
+
+def frame_seed(f: int) -> int:
+    return FRAME_SEED0 + f
+
+
+def pack_bits(bits: np.ndarray) -> np.ndarray:
+    """0/1 bytes -> uint32 words, bit v in word v // 32 at position v % 32."""
+    bits = np.asarray(bits, dtype=np.uint8) & 1
+    nw = (bits.shape[-1] + 31) // 32
+    pad = np.zeros(bits.shape[:-1] + (nw * 32,), dtype=np.uint8)
+    pad[..., : bits.shape[-1]] = bits
+    w = pad.reshape(bits.shape[:-1] + (nw, 32)).astype(np.uint64)
+    words = (w << np.arange(32, dtype=np.uint64)).sum(axis=-1)
+    return words.astype(np.uint32)
+
+
+def unpack_bits(words: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of ``pack_bits``."""
+    words = np.asarray(words, dtype=np.uint32)
+    b = (words[..., :, None] >> np.arange(32, dtype=np.uint32)) & 1
+    return b.reshape(words.shape[:-1] + (-1,))[..., :n].astype(np.uint8)
+
+
+@dataclass(frozen=True)
+class Workload:
+    """A named synthetic workload (code recipe + channel + iteration budget)."""
+    name: str
+    Z: int
+    snr: float
+    max_iter: int
+    frames: int
+    et: bool
+    rate: str = "0.02"
+    extra: dict = field(default_factory=dict)
+
+    def code(self) -> dict:
+        return {"0.02": rate002_code, "0.05": rate005_code,
+                "0.10": rate010_code}[self.rate](self.Z)
+
+
+# Rate 0.02, Z=512 (n = 25,600), SNR 0.029, 50 fixed iterations.
+SINGLE_FRAME_Z512 = Workload("rate0.02_n25600_snr0.029_50it", 512, 0.029, 50, 1, False)
+# Rate 0.02, Z=20,000 (n = 10^6), SNR 0.029, up to 500 iterations with stop test.
+PAPER_SCALE_Z20000 = Workload("rate0.02_n1e6_snr0.029_500it", 20000, 0.029, 500, 16, True)
