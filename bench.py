@@ -1,0 +1,466 @@
+#!/usr/bin/env python3
+"""Raw decoded throughput of QC-LDPC reverse reconciliation on one or more GB300s.
+
+Workload (the paper-scale case): rate-0.02 QC multi-edge code, 49x50 base,
+Z = 20,000 (n = 10^6), 8-D reconciliation LLRs at SNR 0.029, flooding
+sum-product with the stop test after every iteration, at most 500 iterations.
+One step = the whole hot path over one batch of 16 frames resident in HBM:
+qcldpc_llr_8d (8-D map) followed by qcldpc_decode (message passing, stop test,
+key bits). Code construction (host tables) happens once, before timing.
+
+Metric: raw decoded Mbit/s = bits of all decoded frames / wall time (the raw
+throughput of Sec. IV, timed end to end instead of per iteration). Also
+reported: FER (frame error iff the key bits differ from Bob's, Wilson 95 %),
+information throughput raw * R * (1 - FER), mean iterations, p50/p99 step
+latency. Multi-GPU: independent replicas (frames shard with no exchange),
+weak scaling.
+
+``--impl reference`` times the FP64 CPU oracle instead, on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "rate0.02_n1e6_snr0.029_max500it_16frames"
+METRIC = "raw decoded Mbit/s (rate 0.02, n=1e6)"
+UNIT = "Mbit/s"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--frames", type=int, default=16, help="frames per step")
+    ap.add_argument("--batches", type=int, default=4, help="distinct batches cycled")
+    ap.add_argument("--Z", type=int, default=20000)
+    ap.add_argument("--snr", type=float, default=0.029)
+    ap.add_argument("--max-iter", type=int, default=500)
+    ap.add_argument("--cpu-iters", type=int, default=12,
+                    help="oracle iterations timed for the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--reps", type=int, default=20, help="replays per pass for the roofline")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def wilson(k, n, z=1.96):
+    if n == 0:
+        return (float("nan"), float("nan"))
+    p = k / n
+    d = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return (max(0.0, c - h), min(1.0, c + h))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": HBM_FALLBACK_GBS}, "fallback"
+
+
+# ------------------------------------------------------------ clock sampler
+
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.5)
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        inside = [r for r in rows if self.t0 - 0.2 <= r[0] <= self.t1 + 0.2] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v == "Active"})
+        sm = [r[1] for r in inside]
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(r[2] for r in inside) if inside else None,
+                "reasons": reasons, "samples": len(inside)}
+
+
+# ------------------------------------------------------- algorithmic bytes
+
+def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int):
+    """Bytes one frame's check-node / variable-node pass must move (FP32).
+
+    Check pass: read and write every heavy message (n_h Z floats each way),
+    read the degree-1 Phi values (n_d1 Z floats), the heavy posteriors once
+    (n_hcols Z floats), the syndrome (mb Z bits) and previous degree-1
+    decisions (n_d1 Z bits), write new decisions (n_d1 Z bits).
+    Variable pass: read every heavy message once, the heavy channel LLRs, and
+    write the heavy posteriors.
+    """
+    cn = 4 * (2 * n_h * Z + n_d1 * Z + n_hcols * Z) + (mb * Z + 2 * n_d1 * Z) / 8
+    vn = 4 * (n_h * Z + 2 * n_hcols * Z)
+    return cn, vn
+
+
+def iteration_bytes_survey(Z):
+    """Per-frame algorithmic bytes of one flooding iteration: heavy messages
+    read+write once (119 Z * 8), degree-1 LLRs (48 Z * 4), heavy Q and
+    posterior (2 Z * 12), syndrome (49 Z / 8)."""
+    return 119 * Z * 8 + 48 * Z * 4 + 2 * Z * 12 + 49 * Z / 8
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("decode.cu", "qcldpc_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1702_07740_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(Z, snr, iters, seed):
+    """Time the FP64 oracle on one frame: 8-D map plus `iters` iterations."""
+    import oracle
+    d = synth.rate002_code(Z)
+    code = oracle.Code.from_dict(d)
+    x, y, bits = synth.channel_frame(code.n, snr, seed)
+    m32 = oracle.bob_message(y, bits).astype(np.float32)
+    syn = oracle.syndrome(code, bits)
+    x64, m64 = x.astype(np.float32).astype(np.float64), m32.astype(np.float64)
+    t0 = time.perf_counter()
+    q = oracle.llr(x64, m64, snr)
+    t1 = time.perf_counter()
+    oracle.decode(code, q, syn, iters, et_start=iters + 1)
+    t2 = time.perf_counter()
+    return code.n, t1 - t0, (t2 - t1) / max(iters, 1)
+
+
+def oracle_rate(n, t_map, t_iter, iters_per_frame):
+    """Raw Mbit/s of the oracle, extrapolated to iters_per_frame iterations."""
+    return n / (t_map + t_iter * iters_per_frame) / 1e6
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    sample_iters = 2
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        n, t_map, t_iter = oracle_sample(args.Z, args.snr, sample_iters, synth.frame_seed(s))
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append((n, t_map, t_iter, dt))
+    t_map = float(np.mean([t[1] for t in times]))
+    t_iter = float(np.mean([t[2] for t in times]))
+    n = times[0][0]
+    value = oracle_rate(n, t_map, t_iter, args.max_iter)
+    sample = (f"per step: 1 frame (n={n}), 8-D map + {sample_iters} flooding iterations of the "
+              f"FP64 oracle, extrapolated to {args.max_iter} iterations per frame")
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean([t[3] for t in times])),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "snr": args.snr,
+                   "max_iter": args.max_iter},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_1702_07740_gb300 import qcldpc as q
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    q.load()
+    stream = torch.cuda.current_stream()
+
+    d = synth.rate002_code(args.Z)
+    code = q.create_code_from(d)
+    n, k, F, B = code.n, code.k, args.frames, args.batches
+    wm, wk = (code.m + 31) // 32, (k + 31) // 32
+    params = q.qcldpc_params_init()
+
+    # --- seeded inputs, resident in HBM before timing
+    host = []
+    batches = []
+    for b in range(B):
+        xs, ys, bs = [], [], []
+        for f in range(F):
+            seed = synth.frame_seed((rank * B + b) * F + f)
+            x, y, bits = synth.channel_frame(n, args.snr, seed)
+            xs.append(x.astype(np.float32)); ys.append(y.astype(np.float32)); bs.append(bits)
+        x_h = torch.from_numpy(np.concatenate(xs)).pin_memory()
+        y_d = torch.from_numpy(np.concatenate(ys)).to(dev)
+        bits_np = np.stack(bs)
+        bits_d = torch.from_numpy(synth.pack_bits(bits_np).view(np.int32).reshape(-1)).to(dev)
+        m_d = torch.empty(F * n, dtype=torch.float32, device=dev)
+        syn_d = torch.empty(F * wm, dtype=torch.int32, device=dev)
+        # Bob's side: public message M = U Y and syndrome s = H C (GPU, untimed)
+        q.qcldpc_bob_message_8d(y_d, bits_d, F * n, m_d)
+        q.qcldpc_syndrome(code, bits_d, syn_d, F)
+        del y_d, bits_d
+        batches.append({
+            "x": x_h.to(dev), "m": m_d, "syn": syn_d,
+            "keys": torch.zeros(F * wk, dtype=torch.int32, device=dev),
+            "conv": torch.zeros(F, dtype=torch.int32, device=dev),
+            "iters": torch.zeros(F, dtype=torch.int32, device=dev),
+        })
+        host.append({"x": x_h, "m": m_d.cpu().pin_memory(), "syn": syn_d.cpu().pin_memory(),
+                     "key_ref": bits_np[:, :k]})
+    torch.cuda.synchronize()
+    llr = torch.empty(F * n, dtype=torch.float32, device=dev)
+    ws_bytes = q.qcldpc_decode_workspace(code, F, params)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+
+    def step(bt):
+        q.qcldpc_llr_8d(bt["x"], bt["m"], F * n, args.snr, llr, stream)
+        q.qcldpc_decode(code, llr, bt["syn"], F, args.max_iter, params, bt["keys"], bt["conv"],
+                        bt["iters"], ws, ws_bytes, stream)
+
+    for s in range(args.warmup):
+        step(batches[s % B])
+    torch.cuda.synchronize()
+
+    # --- timed region: device-resident inputs
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if sampler:
+        sampler.mark(True)
+    evs[0].record(stream)
+    for s in range(args.steps):
+        step(batches[s % B])
+        evs[s + 1].record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.mark(False)
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    clocks = sampler.stop() if sampler else None
+    value = world * args.steps * F * n / elapsed / 1e6
+
+    # --- accuracy and launch count (deterministic: a batch decodes identically each time)
+    frame_err = conv_n = 0
+    iters_all = []
+    loop_passes = []
+    for b in range(B):
+        keys = synth.unpack_bits(batches[b]["keys"].cpu().numpy().view(np.uint32).reshape(F, wk), k)
+        conv = batches[b]["conv"].cpu().numpy()
+        its = batches[b]["iters"].cpu().numpy()
+        frame_err += int((keys != host[b]["key_ref"]).any(axis=1).sum())
+        conv_n += int(conv.sum())
+        iters_all.extend(its.tolist())
+        loop_passes.append(int(its.max()) + 1)
+    frames_total = B * F
+    fer = frame_err / frames_total
+    launches = sum(1 + 3 + 3 * loop_passes[s % B] for s in range(args.steps))
+
+    # --- end to end: pinned host inputs -> device -> keys/flags back to host
+    stage = {"x": torch.empty(F * n, dtype=torch.float32, device=dev),
+             "m": torch.empty(F * n, dtype=torch.float32, device=dev),
+             "syn": torch.empty(F * wm, dtype=torch.int32, device=dev)}
+    outs_h = [{"keys": torch.empty(F * wk, dtype=torch.int32).pin_memory(),
+               "conv": torch.empty(F, dtype=torch.int32).pin_memory(),
+               "iters": torch.empty(F, dtype=torch.int32).pin_memory()} for _ in range(B)]
+
+    def e2e_step(s):
+        hb, bt, oh = host[s % B], batches[s % B], outs_h[s % B]
+        stage["x"].copy_(hb["x"], non_blocking=True)
+        stage["m"].copy_(hb["m"], non_blocking=True)
+        stage["syn"].copy_(hb["syn"], non_blocking=True)
+        q.qcldpc_llr_8d(stage["x"], stage["m"], F * n, args.snr, llr, stream)
+        q.qcldpc_decode(code, llr, stage["syn"], F, args.max_iter, params, bt["keys"], bt["conv"],
+                        bt["iters"], ws, ws_bytes, stream)
+        oh["keys"].copy_(bt["keys"], non_blocking=True)
+        oh["conv"].copy_(bt["conv"], non_blocking=True)
+        oh["iters"].copy_(bt["iters"], non_blocking=True)
+
+    for s in range(min(args.warmup, 2)):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        e2e_step(s)
+    e1.record(stream)
+    e1.synchronize()
+    e2e_elapsed = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_elapsed = float(t.item())
+    e2e_value = world * args.steps * F * n / e2e_elapsed / 1e6
+    h2d = 2 * F * n * 4 + F * wm * 4
+    d2h = F * wk * 4 + 2 * F * 4
+
+    # --- roofline of the dominant pass (replayed with the decode's launch shape)
+    q.qcldpc_decode(code, llr, batches[0]["syn"], F, args.max_iter, params, batches[0]["keys"],
+                    batches[0]["conv"], batches[0]["iters"], ws, ws_bytes, stream)
+    cn_ms, vn_ms = q.qcldpc_time_passes(code, F, ws, ws_bytes, args.reps, stream)
+    col_count = np.bincount(d["col"], minlength=d["nb"])
+    heavy = col_count != 1
+    cn_b, vn_b = pass_bytes(args.Z, n_h=int(heavy[d["col"]].sum()),
+                            n_d1=int((~heavy[d["col"]]).sum()), n_hcols=int(heavy.sum()),
+                            mb=d["mb"])
+    peaks, peak_kind = measured_peaks()
+    dom, dom_ms, dom_bytes = (("cn_kernel", cn_ms, cn_b * F) if cn_ms >= vn_ms
+                              else ("vn_kernel", vn_ms, vn_b * F))
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = ncu_traffic(dom)
+    iter_ms = cn_ms + vn_ms
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # --- CPU oracle baseline (rank 0, one GPU only)
+    cpu = None
+    mean_iters = float(np.mean(iters_all))
+    if world == 1 and not args.no_cpu_baseline:
+        nn, t_map, t_iter = oracle_sample(args.Z, args.snr, args.cpu_iters, synth.frame_seed(0))
+        cpu = {"value": oracle_rate(nn, t_map, t_iter, mean_iters), "unit": UNIT, "cores": 1,
+               "kind": "oracle",
+               "sample": (f"1 frame (n={nn}): FP64 8-D map + {args.cpu_iters} flooding "
+                          f"iterations, extrapolated to the GPU run's mean {mean_iters:.1f} "
+                          f"iterations per frame; single-threaded C")}
+
+    lo, hi = wilson(frame_err, frames_total)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "k": k, "snr": args.snr,
+                   "frames_per_step": F, "distinct_frames": frames_total,
+                   "max_iter": args.max_iter, "stop_test": "after every iteration",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "no flush: per-iteration working set "
+                         f"{F * (cn_b + vn_b) / 1e6:.0f} MB > 129 MB L2"},
+        "fer": fer, "fer_wilson95": [lo, hi], "frames_converged": conv_n,
+        "info_mbps": value * (k / n) * (1 - fer), "mean_iters": mean_iters,
+        "step_ms_p50": float(np.percentile(step_ms, 50)),
+        "step_ms_p99": float(np.percentile(step_ms, 99)),
+        "iteration_us_per_frame": iter_ms * 1e3 / F,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "cn_ms": cn_ms, "vn_ms": vn_ms,
+                     "bytes_per_launch": dom_bytes},
+        "clocks": clocks,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,218 @@
+/*
+ * qcldpc — GB300 (sm_103a) decoder for quasi-cyclic multi-edge LDPC codes used
+ * in long-distance CV-QKD reverse reconciliation (arXiv 1702.07740).
+ *
+ * C ABI. Every device buffer is owned by the caller; the library never
+ * allocates device memory, never frees or synchronises caller memory, and
+ * every call that takes a stream only enqueues work on it. Calls return 0 on success or a
+ * negative QCLDPC_E_* status; qcldpc_last_error() then describes the failure
+ * (thread-local text, valid until the next failing call on the same thread).
+ * A frame that does not converge is not an error: its converged flag is 0.
+ *
+ * Bit packing: bit v of a frame is bit (v % 32) of 32-bit word v / 32
+ * (LSB first). Frames of a batch are stored back to back; each packed frame
+ * occupies ceil(bits / 32) words. Float arrays are frame-major, n floats per
+ * frame.
+ *
+ * LLR sign convention: Q_v = ln P(C_v = 0) / P(C_v = 1) (Algorithm 1, Step 1).
+ */
+#ifndef QCLDPC_H
+#define QCLDPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qcldpc_stream_t; /* = cudaStream_t; NULL = legacy default stream */
+
+enum {
+    QCLDPC_OK = 0,
+    QCLDPC_E_INVAL = -1,       /* bad argument (null pointer, size, range) */
+    QCLDPC_E_SHIFT_RANGE = -2, /* circulant shift outside [0, Z) */
+    QCLDPC_E_DUP_SHIFT = -3,   /* two circulants with equal shift in one base entry */
+    QCLDPC_E_ALIGN = -4,       /* pointer not aligned as required */
+    QCLDPC_E_NOMEM = -5,       /* host allocation failed or workspace too small */
+    QCLDPC_E_CUDA = -6,        /* a CUDA runtime call failed */
+    QCLDPC_E_TIMEOUT = -7,     /* reserved: a bounded device wait gave up */
+    QCLDPC_E_UNSUPPORTED = -8  /* code exceeds a compile-time table limit */
+};
+
+/* Compile-time table limits of this build (checked by qcldpc_create_code). */
+#define QCLDPC_MAX_BASE_ROWS 128
+#define QCLDPC_MAX_BASE_COLS 512
+#define QCLDPC_MAX_CIRCULANTS 512
+#define QCLDPC_MAX_HEAVY_COLS 32
+#define QCLDPC_MAX_ROW_DEGREE 16
+#define QCLDPC_MAX_Z (1 << 24)
+
+typedef struct qcldpc_code qcldpc_code; /* opaque, library-owned */
+
+/*
+ * Build a QC code from its base-matrix circulant list (Sec. III-D: every base
+ * entry of value i is replaced by the Z x Z identity shifted right by i-1).
+ * Circulant h = (circ_row[h], circ_col[h], circ_shift[h]) puts, for every
+ * i in [0, Z), a one at (check circ_row*Z + i, variable circ_col*Z +
+ * (i + circ_shift) mod Z). Several circulants may share a base entry if their
+ * shifts differ (equal shifts would cancel over GF(2): QCLDPC_E_DUP_SHIFT).
+ *
+ *   mb, nb      base rows / columns; n = nb*Z bits, m = mb*Z checks, k = n-m
+ *   Z           expansion factor (lifting size), 1 <= Z <= QCLDPC_MAX_Z
+ *   n_circ      number of circulants (1..QCLDPC_MAX_CIRCULANTS)
+ *   circ_*      HOST arrays of n_circ int32; copied, caller keeps ownership
+ *   out         receives the new handle (set to NULL on failure)
+ *
+ * Columns holding exactly one circulant are degree-1 ("diagonal") columns:
+ * their variable nodes never need per-iteration messages (Sec. III-D). All
+ * other columns are heavy columns. Host-only: the tables travel to the GPU
+ * as kernel parameters, so no device memory is allocated. The handle
+ * remembers the CUDA device current at creation (decoding on another device
+ * fails with QCLDPC_E_INVAL). Errors: QCLDPC_E_INVAL, _SHIFT_RANGE,
+ * _DUP_SHIFT, _UNSUPPORTED, _NOMEM.
+ */
+int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
+                       const int32_t *circ_row, const int32_t *circ_col,
+                       const int32_t *circ_shift, qcldpc_code **out);
+
+/* Release a handle (NULL is ignored). Work already enqueued that uses it
+ * must have completed. */
+void qcldpc_destroy_code(qcldpc_code *code);
+
+/* Sizes of a code: n bits, m checks, k = n - m key bits, n_edges ones in H.
+ * Any output pointer may be NULL. Errors: QCLDPC_E_INVAL. */
+int qcldpc_code_info(const qcldpc_code *code, int64_t *n, int64_t *m,
+                     int64_t *k, int64_t *n_edges);
+
+/*
+ * Syndrome s = H x (mod 2) of n_frames frames (the Slepian-Wolf form of
+ * reverse reconciliation, Sec. II-C: Bob publishes s for his bits).
+ *   bits_dev   DEVICE uint32[n_frames * ceil(n/32)], packed frames
+ *   syn_dev    DEVICE uint32[n_frames * ceil(m/32)], packed output
+ * Bit-exact. Errors: QCLDPC_E_INVAL, _ALIGN (4-byte), _CUDA (launch).
+ */
+int qcldpc_syndrome(const qcldpc_code *code, const uint32_t *bits_dev,
+                    uint32_t *syn_dev, int n_frames, qcldpc_stream_t stream);
+
+/*
+ * Bob's side of 8-dimensional reconciliation (Sec. II-C): per block b of
+ * eight positions, U_j = (-1)^{C_{8b+j}} and M = U Y, the octonion product
+ * (Cayley-Dickson doubling, (p,q)(r,s) = (pr - conj(s) q, sp + q conj(r))).
+ *   y_dev     DEVICE float[n], Bob's normalised Gaussian samples
+ *   bits_dev  DEVICE uint32[ceil(n/32)], packed bits C
+ *   n         total length, n % 8 == 0 (frames may be concatenated if each
+ *             frame length is a multiple of 8 and of 32)
+ *   m_dev     DEVICE float[n], the public message M
+ * FP32 arithmetic. Errors: QCLDPC_E_INVAL, _ALIGN (16-byte floats), _CUDA.
+ */
+int qcldpc_bob_message_8d(const float *y_dev, const uint32_t *bits_dev,
+                          int64_t n, float *m_dev, qcldpc_stream_t stream);
+
+/*
+ * Alice's channel LLRs for 8-dimensional reconciliation (Sec. II-C and
+ * Step 1 of Algorithm 1): R = M X^{-1} = (M conj(X)) / |X|^2 and the virtual
+ * BIAWGN noise variance sigma_N^2 = 8 sigma_Z^2 / |X|^2 with sigma_Z^2 =
+ * 1/snr, so Q = 2 R / sigma_N^2 = (M conj(X)) * snr / 4.
+ *   x_dev, m_dev   DEVICE float[n] (Alice's X, Bob's message M)
+ *   n              n % 8 == 0
+ *   snr            > 0
+ *   llr_dev        DEVICE float[n] output Q
+ * FP32 arithmetic. Errors: QCLDPC_E_INVAL, _ALIGN (16-byte), _CUDA.
+ */
+int qcldpc_llr_8d(const float *x_dev, const float *m_dev, int64_t n, float snr,
+                  float *llr_dev, qcldpc_stream_t stream);
+
+/* Decoder options. Initialise with qcldpc_params_init. */
+typedef struct qcldpc_params {
+    float clip;          /* every edge message is clipped to [-clip, clip];
+                            <= 0 disables clipping. Default 15 */
+    float phi_floor;     /* every Phi argument is floored at this value
+                            (Phi(x) = -ln tanh(x/2)). Default 1e-6 */
+    int32_t et_start;    /* the stop test H C = s runs after iteration t when
+                            t >= et_start, and always after the last
+                            iteration (delayed early termination, Sec. IV-A).
+                            Default 1 */
+    int32_t schedule;    /* 0 = flooding (the only schedule of this build) */
+    int32_t msg_format;  /* 0 = FP32 edge messages (the only format yet) */
+    int32_t soft_output; /* 1: reserve workspace for qcldpc_decode_soft */
+    int32_t reserved[2]; /* must be zero */
+} qcldpc_params;
+
+void qcldpc_params_init(qcldpc_params *p);
+
+/* Bytes of device workspace qcldpc_decode needs for n_frames frames
+ * (p may be NULL for defaults). Returns 0 on invalid arguments. */
+size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
+                               const qcldpc_params *p);
+
+/*
+ * Syndrome-form sum-product decoding (Algorithm 1, flooding schedule) of
+ * n_frames independent frames, the whole loop on the device.
+ *
+ * For every frame: L_vc^(0) = Q_v. Iteration t: check nodes send
+ *   m_cv = (-1)^{s_c} prod_{v' != v} sgn(L_v'c) Phi(sum_{v' != v} Phi(|L_v'c|)),
+ * variable nodes form L_v = Q_v + sum_c m_cv and L_vc = L_v - m_cv, and the
+ * hard decision is C_v = 1 iff L_v < 0 (sgn(0) = +1). After iteration t the
+ * stop test H C = s runs when t >= et_start or t = max_iter; a frame that
+ * passes stops there. Messages are clipped to [-clip, clip], Phi arguments
+ * floored at phi_floor, all arithmetic FP32.
+ *
+ *   llr_dev        DEVICE float[n_frames * n], channel LLRs Q (16-byte aligned)
+ *   syn_dev        DEVICE uint32[n_frames * ceil(m/32)], packed syndromes s
+ *   max_iter       >= 0 (0: the channel decisions are tested and returned)
+ *   p              options, NULL for defaults
+ *   key_bits_dev   DEVICE uint32[n_frames * ceil(k/32)]: decisions C_v for
+ *                  v < k (the key S-hat, Step 5: parity bits discarded)
+ *   converged_dev  DEVICE int32[n_frames]: 1 if H C = s at the stop
+ *   iters_dev      DEVICE int32[n_frames]: iteration the frame stopped at
+ *   workspace_dev  DEVICE scratch of at least qcldpc_decode_workspace()
+ *                  bytes, 256-byte aligned; contents are overwritten
+ * Enqueues on `stream`; returns without waiting. Concurrent calls on one code
+ * handle are serialised on the host. Errors: QCLDPC_E_INVAL, _ALIGN, _NOMEM
+ * (workspace too small), _CUDA.
+ */
+int qcldpc_decode(const qcldpc_code *code, const float *llr_dev,
+                  const uint32_t *syn_dev, int n_frames, int max_iter,
+                  const qcldpc_params *p, uint32_t *key_bits_dev,
+                  int32_t *converged_dev, int32_t *iters_dev,
+                  void *workspace_dev, size_t workspace_bytes,
+                  qcldpc_stream_t stream);
+
+/*
+ * As qcldpc_decode, and also writes the posterior LLR L_v of every bit at
+ * the stopping iteration (Algorithm 1, Step 3) to posterior_dev
+ * (DEVICE float[n_frames * n]). Requires p != NULL with p->soft_output = 1
+ * for both this call and qcldpc_decode_workspace.
+ */
+int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
+                       const uint32_t *syn_dev, int n_frames, int max_iter,
+                       const qcldpc_params *p, uint32_t *key_bits_dev,
+                       int32_t *converged_dev, int32_t *iters_dev,
+                       float *posterior_dev, void *workspace_dev,
+                       size_t workspace_bytes, qcldpc_stream_t stream);
+
+/*
+ * Measurement helper; the paper has no counterpart. Replays the check-node
+ * pass and then the variable-node pass of the decoder `reps` times each, with
+ * the launch configuration qcldpc_decode uses, on the state a previous
+ * qcldpc_decode / qcldpc_decode_soft call with the same code, n_frames and
+ * workspace left behind, and returns each pass's mean duration in
+ * milliseconds (CUDA events on `stream`). The replays run as iteration 2 of
+ * a decode with every frame active, so each moves a full iteration's data.
+ * Overwrites the decoder state in the workspace (the last decode's outputs
+ * are untouched). Blocks the calling thread until the replays finish.
+ * Errors: QCLDPC_E_INVAL (no matching previous decode), _NOMEM, _CUDA.
+ */
+int qcldpc_time_passes(const qcldpc_code *code, int n_frames, void *workspace_dev,
+                       size_t workspace_bytes, int reps, float *cn_ms, float *vn_ms,
+                       qcldpc_stream_t stream);
+
+/* Description of the last failure on this thread ("" if none). */
+const char *qcldpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCLDPC_H */

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libqcldpc (include/qcldpc.h). Argument marshalling only.
+
+Every function keeps the C name. Device buffers are torch CUDA tensors (any
+dtype of the right width, contiguous); the stream defaults to torch's current
+stream. All arithmetic runs in the CUDA library: if it is missing or no GPU is
+visible, the compute calls raise instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+QCLDPC_OK = 0
+STATUS = {
+    -1: "QCLDPC_E_INVAL", -2: "QCLDPC_E_SHIFT_RANGE", -3: "QCLDPC_E_DUP_SHIFT",
+    -4: "QCLDPC_E_ALIGN", -5: "QCLDPC_E_NOMEM", -6: "QCLDPC_E_CUDA",
+    -7: "QCLDPC_E_TIMEOUT", -8: "QCLDPC_E_UNSUPPORTED",
+}
+
+# Every symbol include/qcldpc.h declares.
+EXPORTED = [
+    "qcldpc_create_code", "qcldpc_destroy_code", "qcldpc_code_info",
+    "qcldpc_syndrome", "qcldpc_bob_message_8d", "qcldpc_llr_8d",
+    "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
+    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_last_error",
+]
+
+
+class QcldpcError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+class qcldpc_params(ctypes.Structure):
+    _fields_ = [
+        ("clip", ctypes.c_float),
+        ("phi_floor", ctypes.c_float),
+        ("et_start", ctypes.c_int32),
+        ("schedule", ctypes.c_int32),
+        ("msg_format", ctypes.c_int32),
+        ("soft_output", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqcldpc.so (building it with nvcc first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libqcldpc.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        lib.qcldpc_create_code.argtypes = [i32, i32, i32, i32, vp, vp, vp, ctypes.POINTER(vp)]
+        lib.qcldpc_create_code.restype = i32
+        lib.qcldpc_destroy_code.argtypes = [vp]
+        lib.qcldpc_destroy_code.restype = None
+        lib.qcldpc_code_info.argtypes = [vp, vp, vp, vp, vp]
+        lib.qcldpc_code_info.restype = i32
+        lib.qcldpc_syndrome.argtypes = [vp, vp, vp, i32, vp]
+        lib.qcldpc_syndrome.restype = i32
+        lib.qcldpc_bob_message_8d.argtypes = [vp, vp, i64, vp, vp]
+        lib.qcldpc_bob_message_8d.restype = i32
+        lib.qcldpc_llr_8d.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp]
+        lib.qcldpc_llr_8d.restype = i32
+        lib.qcldpc_params_init.argtypes = [ctypes.POINTER(qcldpc_params)]
+        lib.qcldpc_params_init.restype = None
+        lib.qcldpc_decode_workspace.argtypes = [vp, i32, ctypes.POINTER(qcldpc_params)]
+        lib.qcldpc_decode_workspace.restype = sz
+        lib.qcldpc_decode.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
+                                      vp, vp, vp, vp, sz, vp]
+        lib.qcldpc_decode.restype = i32
+        lib.qcldpc_decode_soft.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
+                                           vp, vp, vp, vp, vp, sz, vp]
+        lib.qcldpc_decode_soft.restype = i32
+        lib.qcldpc_time_passes.argtypes = [vp, i32, vp, sz, i32, ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float), vp]
+        lib.qcldpc_time_passes.restype = i32
+        lib.qcldpc_last_error.argtypes = []
+        lib.qcldpc_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def qcldpc_last_error() -> str:
+    return load().qcldpc_last_error().decode()
+
+
+def _check(status: int, where: str):
+    if status != QCLDPC_OK:
+        raise QcldpcError(status, where, qcldpc_last_error())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, nbytes_elem=None, name="buffer"):
+    """Device pointer of a contiguous CUDA tensor (argument check only)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if nbytes_elem is not None and t.element_size() != nbytes_elem:
+        raise TypeError(f"{name} must have {nbytes_elem}-byte elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def qcldpc_params_init(**overrides) -> qcldpc_params:
+    p = qcldpc_params()
+    load().qcldpc_params_init(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+class Code:
+    """Owning wrapper of a qcldpc_code handle."""
+
+    def __init__(self, handle, mb, nb, Z):
+        self._h = handle
+        self.mb, self.nb, self.Z = mb, nb, Z
+        self.n, self.m, self.k, self.n_edges = qcldpc_code_info(self)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and _lib is not None:
+            _lib.qcldpc_destroy_code(h)
+
+
+def qcldpc_create_code(mb, nb, Z, circ_row, circ_col, circ_shift) -> Code:
+    row = np.ascontiguousarray(circ_row, dtype=np.int32)
+    col = np.ascontiguousarray(circ_col, dtype=np.int32)
+    shift = np.ascontiguousarray(circ_shift, dtype=np.int32)
+    if not (row.shape == col.shape == shift.shape) or row.ndim != 1:
+        raise ValueError("circulant arrays must be 1-D and of equal length")
+    out = ctypes.c_void_p()
+    st = load().qcldpc_create_code(int(mb), int(nb), int(Z), int(row.shape[0]),
+                                   row.ctypes.data_as(ctypes.c_void_p),
+                                   col.ctypes.data_as(ctypes.c_void_p),
+                                   shift.ctypes.data_as(ctypes.c_void_p), ctypes.byref(out))
+    _check(st, "qcldpc_create_code")
+    return Code(out, int(mb), int(nb), int(Z))
+
+
+def create_code_from(d: dict) -> Code:
+    return qcldpc_create_code(d["mb"], d["nb"], d["Z"], d["row"], d["col"], d["shift"])
+
+
+def qcldpc_destroy_code(code: Code):
+    h, code._h = code._h, None
+    if h is not None:
+        load().qcldpc_destroy_code(h)
+
+
+def qcldpc_code_info(code: Code):
+    vals = [ctypes.c_int64() for _ in range(4)]
+    st = load().qcldpc_code_info(code.handle, *[ctypes.byref(v) for v in vals])
+    _check(st, "qcldpc_code_info")
+    return tuple(v.value for v in vals)
+
+
+def qcldpc_syndrome(code: Code, bits_dev, syn_dev, n_frames: int, stream=None):
+    st = load().qcldpc_syndrome(code.handle, _dev(bits_dev, 4, "bits_dev"),
+                                _dev(syn_dev, 4, "syn_dev"), int(n_frames), _stream(stream))
+    _check(st, "qcldpc_syndrome")
+
+
+def qcldpc_bob_message_8d(y_dev, bits_dev, n: int, m_dev, stream=None):
+    st = load().qcldpc_bob_message_8d(_dev(y_dev, 4, "y_dev"), _dev(bits_dev, 4, "bits_dev"),
+                                      int(n), _dev(m_dev, 4, "m_dev"), _stream(stream))
+    _check(st, "qcldpc_bob_message_8d")
+
+
+def qcldpc_llr_8d(x_dev, m_dev, n: int, snr: float, llr_dev, stream=None):
+    st = load().qcldpc_llr_8d(_dev(x_dev, 4, "x_dev"), _dev(m_dev, 4, "m_dev"), int(n),
+                              float(snr), _dev(llr_dev, 4, "llr_dev"), _stream(stream))
+    _check(st, "qcldpc_llr_8d")
+
+
+def qcldpc_decode_workspace(code: Code, n_frames: int, params: qcldpc_params | None = None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    return int(load().qcldpc_decode_workspace(code.handle, int(n_frames), p))
+
+
+def qcldpc_decode(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,
+                  params: qcldpc_params | None, key_bits_dev, converged_dev, iters_dev,
+                  workspace_dev, workspace_bytes: int, stream=None):
+    p = ctypes.byref(params) if params is not None else None
+    st = load().qcldpc_decode(code.handle, _dev(llr_dev, 4, "llr_dev"),
+                              _dev(syn_dev, 4, "syn_dev"), int(n_frames), int(max_iter), p,
+                              _dev(key_bits_dev, 4, "key_bits_dev"),
+                              _dev(converged_dev, 4, "converged_dev"),
+                              _dev(iters_dev, 4, "iters_dev"), _dev(workspace_dev, None, "workspace"),
+                              int(workspace_bytes), _stream(stream))
+    _check(st, "qcldpc_decode")
+
+
+def qcldpc_decode_soft(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,
+                       params: qcldpc_params, key_bits_dev, converged_dev, iters_dev,
+                       posterior_dev, workspace_dev, workspace_bytes: int, stream=None):
+    st = load().qcldpc_decode_soft(code.handle, _dev(llr_dev, 4, "llr_dev"),
+                                   _dev(syn_dev, 4, "syn_dev"), int(n_frames), int(max_iter),
+                                   ctypes.byref(params), _dev(key_bits_dev, 4, "key_bits_dev"),
+                                   _dev(converged_dev, 4, "converged_dev"),
+                                   _dev(iters_dev, 4, "iters_dev"),
+                                   _dev(posterior_dev, 4, "posterior_dev"),
+                                   _dev(workspace_dev, None, "workspace"), int(workspace_bytes),
+                                   _stream(stream))
+    _check(st, "qcldpc_decode_soft")
+
+
+def qcldpc_time_passes(code: Code, n_frames: int, workspace_dev, workspace_bytes: int,
+                       reps: int, stream=None):
+    """Mean (check-node ms, variable-node ms) of replayed decoder passes."""
+    cn, vn = ctypes.c_float(), ctypes.c_float()
+    st = load().qcldpc_time_passes(code.handle, int(n_frames), _dev(workspace_dev, None, "workspace"),
+                                   int(workspace_bytes), int(reps), ctypes.byref(cn),
+                                   ctypes.byref(vn), _stream(stream))
+    _check(st, "qcldpc_time_passes")
+    return cn.value, vn.value
+
+
+class Decoder:
+    """Convenience owner of the device buffers one decode batch needs.
+
+    Holds the code, a workspace and the output tensors for ``n_frames``
+    frames; ``decode`` enqueues ``qcldpc_decode`` (or the soft variant).
+    """
+
+    def __init__(self, code: Code, n_frames: int, params: qcldpc_params | None = None,
+                 soft: bool = False, device=None):
+        import torch
+        self.code = code
+        self.n_frames = int(n_frames)
+        self.params = params if params is not None else qcldpc_params_init()
+        if soft:
+            self.params.soft_output = 1
+        self.soft = soft
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.ws_bytes = qcldpc_decode_workspace(code, self.n_frames, self.params)
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        wk = (code.k + 31) // 32
+        self.keys = torch.zeros(self.n_frames * wk, dtype=torch.int32, device=dev)
+        self.converged = torch.zeros(self.n_frames, dtype=torch.int32, device=dev)
+        self.iters = torch.zeros(self.n_frames, dtype=torch.int32, device=dev)
+        self.posterior = (torch.zeros(self.n_frames * code.n, dtype=torch.float32, device=dev)
+                          if soft else None)
+
+    def decode(self, llr_dev, syn_dev, max_iter: int, stream=None):
+        if self.soft:
+            qcldpc_decode_soft(self.code, llr_dev, syn_dev, self.n_frames, max_iter,
+                               self.params, self.keys, self.converged, self.iters,
+                               self.posterior, self.workspace, self.ws_bytes, stream)
+        else:
+            qcldpc_decode(self.code, llr_dev, syn_dev, self.n_frames, max_iter, self.params,
+                          self.keys, self.converged, self.iters, self.workspace,
+                          self.ws_bytes, stream)
