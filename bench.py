@@ -57,6 +57,8 @@ def parse_args():
                     help="oracle iterations timed for the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--reps", type=int, default=20, help="replays per pass for the roofline")
+    ap.add_argument("--launch-mode", choices=["graph", "stream"], default="graph",
+                    help="stream: host-enqueued passes, for profilers only (not a bench number)")
     return ap.parse_args()
 
 
@@ -261,7 +263,7 @@ def run_ours(args, world, rank, local):
     code = q.create_code_from(d)
     n, k, F, B = code.n, code.k, args.frames, args.batches
     wm, wk = (code.m + 31) // 32, (k + 31) // 32
-    params = q.qcldpc_params_init()
+    params = q.qcldpc_params_init(launch_mode=1 if args.launch_mode == "stream" else 0)
 
     # --- seeded inputs, resident in HBM before timing
     host = []

@@ -136,7 +136,14 @@ typedef struct qcldpc_params {
     int32_t schedule;    /* 0 = flooding (the only schedule of this build) */
     int32_t msg_format;  /* 0 = FP32 edge messages (the only format yet) */
     int32_t soft_output; /* 1: reserve workspace for qcldpc_decode_soft */
-    int32_t reserved[2]; /* must be zero */
+    int32_t launch_mode; /* 0: the iteration loop runs inside one CUDA graph
+                            (a conditional WHILE node; no host work per
+                            iteration). 1: the host enqueues max_iter + 1
+                            iteration passes as ordinary kernel launches on
+                            the stream (passes after every frame stopped exit
+                            at once); same results, meant for profilers that
+                            cannot look inside conditional graphs. Default 0 */
+    int32_t reserved;    /* must be zero */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);

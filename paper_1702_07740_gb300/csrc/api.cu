@@ -45,6 +45,8 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->schedule = 0;
     p->msg_format = 0;
     p->soft_output = 0;
+    p->launch_mode = 0;
+    p->reserved = 0;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
@@ -63,8 +65,10 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
         return fail(QCLDPC_E_UNSUPPORTED,
                     "create_code: base matrix, circulant count or Z above the table limits");
     const int64_t n = (int64_t)nb * Z, m = (int64_t)mb * Z;
-    if (n > INT32_MAX || m > INT32_MAX)
-        return fail(QCLDPC_E_UNSUPPORTED, "create_code: n or m above 2^31-1");
+    // Offsets inside one frame's arrays are 32-bit: every array (n_circ Z
+    // messages, 2Z per heavy posterior row) and n, m stay below 2^30.
+    if (n > (1 << 30) || m > (1 << 30) || (int64_t)n_circ * Z > (1 << 29))
+        return fail(QCLDPC_E_UNSUPPORTED, "create_code: n, m or n_circ * Z too large");
 
     std::vector<int> col_count(nb, 0), row_count(mb, 0);
     for (int h = 0; h < n_circ; h++) {
@@ -155,6 +159,17 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
     }
     T.row_ptr[mb] = (uint16_t)pos;
     T.max_row_deg = max_deg;
+    const int ZW = (Z + 31) / 32;
+    for (int q = 0; q < pos; q++) {
+        const RowEnt &e = T.rows[q];
+        if (e.slot >= 0) {
+            T.row_off_a[q] = e.slot * 2 * Z + e.shift;
+            T.row_off_b[q] = e.id * Z;
+        } else {
+            T.row_off_a[q] = e.id * Z;
+            T.row_off_b[q] = e.id * ZW;
+        }
+    }
 
     // Per-heavy-column table in input order.
     pos = 0;
@@ -175,6 +190,9 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
     code->k = T.k;
     code->n_edges = (int64_t)n_circ * Z;
     code->graph_cache = nullptr;
+    code->last_ws = nullptr;
+    code->last_frames = 0;
+    code->last_soft = 0;
     // The tables are passed to kernels by value, so building a code needs no
     // device memory. The handle remembers the current device (-1 when no
     // device is visible: the code can then be inspected but not decoded).

@@ -5,12 +5,16 @@
 // Data layout per frame f (all in the caller's workspace, frame-major):
 //   msg  [n_h][Z]       check-to-variable messages m_cv of every heavy edge,
 //                       indexed by (heavy circulant, check offset i)
-//   L    [n_hcols][Z]   posterior L_v of every heavy variable node
+//   L    [n_hcols][2Z]  posterior L_v of every heavy variable node, stored
+//                       twice in a row so reads at (i + s) need no wrap
 //   phiq [n_d1][Z]      +-Phi(|Q_p|) of every degree-1 variable node, indexed
 //                       by (degree-1 circulant, check offset); its message to
 //                       the check never changes (Sec. III-D, long diagonal)
 //   bits [2][n_d1][ZW]  hard decisions of the degree-1 nodes, double
 //                       buffered by iteration parity (ZW = ceil(Z/32) words)
+// Every array carries kSlack elements of padding at its end, so that lanes
+// past the last check of a row may load without a bounds test (their
+// results are never stored).
 // Degree-1 edges therefore carry no per-iteration state: a check reads its
 // diagonal neighbour's constant Phi value and decides that neighbour's bit
 // itself (Step 4 of Algorithm 1 for degree-1 nodes).
@@ -29,11 +33,22 @@
 //               of m_cv, read at offsets (j - s) mod Z (coalesced, one wrap).
 // A last pass (t = max_iter + 1) runs cn_kernel as a pure stop test.
 //
-// Phi(x) = -ln tanh(x/2) is evaluated in FP32 with the hardware ex2/lg2
-// approximations and two short polynomials (see phi_f below); the FP32 path
-// matches the FP64 oracle's posteriors to ~2e-5 relative after 50 iterations.
+// All call arguments travel as one __grid_constant__ parameter (Work), so
+// they sit in the constant bank as warp-uniform operands; instantiated graphs
+// are cached per distinct argument set.
+//
+// Units: inside the decoder every LLR is kept in base 2, y = x log2(e) for a
+// natural LLR x (L, messages, Phi values, clip and floor). The rule is the
+// same in these units with Phi replaced by psi(y) = log2 coth(y ln2 / 2) (see
+// psi_f), whose exponentials the hardware ex2/lg2 evaluate without argument
+// scaling. Channel LLRs come in and posteriors go out in natural units.
+//
+// psi is evaluated in FP32 with the ex2/lg2 approximations and two short
+// polynomials; the FP32 path matches the FP64 oracle's posteriors to ~2e-5
+// relative after 50 iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <new>
 
 #include "qcldpc_internal.cuh"
@@ -42,13 +57,29 @@ namespace {
 
 using qc::Table;
 
+// Launch shapes (overridable at build time for tuning sweeps). Defaults
+// from a sweep at Z = 20,000 with 16 frames on GB300.
+#ifndef QCLDPC_CN_VPT
+#define QCLDPC_CN_VPT 4
+#endif
+#ifndef QCLDPC_CN_MINBLOCKS
+#define QCLDPC_CN_MINBLOCKS 3
+#endif
+#ifndef QCLDPC_VN_VPT
+#define QCLDPC_VN_VPT 2
+#endif
+#ifndef QCLDPC_VN_UNROLL
+#define QCLDPC_VN_UNROLL 6
+#endif
 constexpr int kThreads = 256;
-constexpr int kCnVpt = 2;  // checks per thread (interleaved by kThreads)
-constexpr int kVnVpt = 2;  // variable nodes per thread
+constexpr int kCnVpt = QCLDPC_CN_VPT;  // checks per thread (interleaved by kThreads)
+constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
+constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
 constexpr int kCtrlThreads = 256;
+constexpr int kSlack = 2048;  // padding elements after every workspace array
+constexpr int kGraphCacheSize = 8;
 
-// Per-call arguments and workspace pointers. Written into the workspace by
-// the first graph node each call; every other node reads it from there.
+// Per-call arguments and workspace pointers (by value in every kernel).
 struct Work {
     const float *llr;      // [F][n]
     const uint32_t *syn;   // [F][words_m]
@@ -60,14 +91,15 @@ struct Work {
     int32_t *active;       // [F]
     int32_t *fail;         // [F] stop-test failures of the current pass
     float *msg;            // [F][n_h][Z]
-    float *L;              // [F][n_hcols][Z]
+    float *L;              // [F][n_hcols][2Z]
     float *phiq;           // [F][n_d1][Z]
     uint32_t *bits;        // [2][F][n_d1][ZW]
     float *post1;          // [2][F][n_d1][Z] (soft output only)
     int64_t n, words_m, words_k;
     int32_t n_frames, max_iter, et_start, soft, ZW;
-    float clip, xmin;
+    float clip, xmin;      // base-2 units
 };
+static_assert(sizeof(Work) <= sizeof(((qcldpc_code *)nullptr)->last_work), "Work too large");
 
 // ---------------------------------------------------------------- Phi
 
@@ -84,57 +116,61 @@ __device__ __forceinline__ float lg2_approx(float x) {
 }
 
 // Polynomial pieces derived by paper_1702_07740_gb300/phi_fit.py.
-constexpr float kG0 = 8.333332092e-02f;
-constexpr float kG1 = -4.860660061e-03f;
-constexpr float kG2 = 3.394155647e-04f;
-constexpr float kG3 = -2.243584640e-05f;
-constexpr float kA1 = 3.333292305e-01f;
-constexpr float kA2 = 2.002381980e-01f;
-constexpr float kA3 = 1.380910724e-01f;
-constexpr float kA4 = 1.488138288e-01f;
+constexpr float kC = 1.528766394e+00f;  // 1 - log2(ln 2)
+constexpr float kG0 = 5.776225403e-02f;
+constexpr float kG1 = -1.618719543e-03f;
+constexpr float kG2 = 5.430740566e-05f;
+constexpr float kG3 = -1.724728236e-06f;
+constexpr float kA0 = 2.885390043e+00f;
+constexpr float kA1 = 9.617848396e-01f;
+constexpr float kA2 = 5.777652860e-01f;
+constexpr float kA3 = 3.984466195e-01f;
+constexpr float kA4 = 4.293859601e-01f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kLog2e = 1.4426950408889634f;
 
-// Phi(x) = -ln tanh(x/2) = ln coth(x/2) for x > 0 (callers floor x).
-//   x <= 1: ln(2/x) + ln(u coth u), u = x/2; the even second term is w G(w).
-//   x >  1: 2 atanh(t), t = e^{-x}; 2 atanh(t) = 2 t A(t^2), A = 1 + v/3 + ...
-// Both branches are evaluated (no divergence); max relative error ~4e-7 for
-// x <= 30 (ex2/lg2 approximations included).
-__device__ __forceinline__ float phi_f(float x) {
-    const float w = x * x;
+// psi(y) = log2 coth(y ln2 / 2) = log2(e) Phi(y ln 2), for y > 0 (callers
+// floor y); Phi(x) = -ln tanh(x/2) is Algorithm 1's check-node function.
+//   small y: psi = 1 - log2(ln 2) - log2(y) + w G(w), w = y^2;
+//   large y: psi = (2/ln 2) atanh(t) = t A(t^2), t = 2^-y.
+// Both pieces are evaluated (no divergence) and combined with a max: each
+// piece underestimates psi outside its own range (split at y = 1/ln 2), so
+// the max picks the accurate piece; they differ only near the split, where
+// both are accurate. Max relative error 2e-7 for y in [1e-6, 60] (ex2/lg2
+// approximations included).
+__device__ __forceinline__ float psi_f(float y) {
+    const float w = y * y;
     const float g = fmaf(fmaf(fmaf(kG3, w, kG2), w, kG1), w, kG0);
-    const float small = fmaf(w, g, kLn2 - kLn2 * lg2_approx(x));
-    const float t = ex2_approx(-x * kLog2e);
+    const float small = fmaf(w, g, kC - lg2_approx(y));
+    const float t = ex2_approx(-y);
     const float v = t * t;
-    const float a = fmaf(fmaf(fmaf(fmaf(kA4, v, kA3), v, kA2), v, kA1), v, 1.0f);
-    const float large = 2.0f * t * a;
-    return x <= 1.0f ? small : large;
+    const float a = fmaf(fmaf(fmaf(fmaf(kA4, v, kA3), v, kA2), v, kA1), v, kA0);
+    return fmaxf(small, t * a);
 }
 
-__device__ __forceinline__ float clampf(float x, float c) { return fminf(fmaxf(x, -c), c); }
+constexpr uint32_t kSign = 0x80000000u;
+__device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 
 // ------------------------------------------------------------ kernels
-
-__global__ void args_kernel(Work w, Work *dst) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = w;
-}
 
 // Initial state: L = Q (heavy), phiq = +-Phi(|clip Q|) and the iteration-0
 // decisions of the degree-1 nodes, frame flags, loop counter t = 1.
 // The message arrays need no initialisation: iteration 1 reads m = 0.
 __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ Table T,
-                                                        const Work *__restrict__ Wp) {
-    const Work W = *Wp;
+                                                        const __grid_constant__ Work W) {
     const int Z = T.Z;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    // heavy posteriors
+    // heavy posteriors in base-2 units (-0 -> +0 so that sgn(0) = +1 everywhere)
     const int64_t nL = (int64_t)W.n_frames * T.n_hcols * Z;
     for (int64_t e = tid; e < nL; e += nthreads) {
         const int64_t f = e / ((int64_t)T.n_hcols * Z);
         const int64_t rem = e - f * T.n_hcols * Z;
         const int hc = (int)(rem / Z), j = (int)(rem - (int64_t)hc * Z);
-        W.L[e] = W.llr[f * W.n + (int64_t)T.hcol_base[hc] * Z + j];
+        const float qv = W.llr[f * W.n + (int64_t)T.hcol_base[hc] * Z + j] * kLog2e + 0.0f;
+        float *row = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+        row[j] = qv;
+        row[j + Z] = qv;
     }
     // degree-1 nodes: one warp per (frame, circulant, 32-check word)
     const int lane = threadIdx.x & 31;
@@ -147,12 +183,11 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
         const int i = wd * 32 + lane;
         bool neg = false;
         if (i < Z) {
-            const int col = T.d1_col[k];
             int vo = i + T.d1_shift[k];
             if (vo >= Z) vo -= Z;
-            const float qv = W.llr[f * W.n + (int64_t)col * Z + vo];
-            const float a = fmaxf(fminf(fabsf(qv), W.clip), W.xmin);
-            const float p = phi_f(a);
+            const float qv = W.llr[f * W.n + (int64_t)T.d1_col[k] * Z + vo];
+            const float a = fmaxf(fminf(fabsf(qv) * kLog2e, W.clip), W.xmin);
+            const float p = psi_f(a);
             const size_t off = ((size_t)f * T.n_d1 + k) * Z + i;
             W.phiq[off] = qv < 0.0f ? -p : p;
             if (W.soft) W.post1[off] = qv;  // iteration-0 posterior, buffer 0
@@ -170,132 +205,305 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
     if (tid == 0) *W.t = 1;
 }
 
-// Check-node pass of iteration t (see the file comment). MAXD bounds the row
-// degree so that every per-edge array stays in registers.
-template <int MAXD>
-__global__ void __launch_bounds__(kThreads) cn_kernel(const __grid_constant__ Table T,
-                                                      const Work *__restrict__ Wp) {
-    const int f = blockIdx.y;
-    if (Wp->active[f] == 0) return;  // block-uniform
-    const int t = *Wp->t;
-    const int max_iter = Wp->max_iter;
-    const bool update = t <= max_iter;
-    const bool check = (t == max_iter + 1) || (t >= 2 && t - 1 >= Wp->et_start);
-    const int Z = T.Z;
-    const int span = kThreads * kCnVpt;
-    const int tiles = (Z + span - 1) / span;
-    const int r = blockIdx.x / tiles;
-    const int i0 = (blockIdx.x - r * tiles) * span + threadIdx.x;
-    const int rp = T.row_ptr[r];
-    const int deg = T.row_ptr[r + 1] - rp;
-    const int nh = T.row_nh[r];
-    const float clip = Wp->clip, xmin = Wp->xmin;
-    const int ZW = Wp->ZW;
-    const int64_t F = Wp->n_frames;
-    float *__restrict__ msg = Wp->msg + (size_t)f * T.n_h * Z;
-    const float *__restrict__ L = Wp->L + (size_t)f * T.n_hcols * Z;
-    const float *__restrict__ phiq = Wp->phiq + (size_t)f * T.n_d1 * Z;
-    uint32_t *__restrict__ bits_cur = Wp->bits + ((size_t)(t & 1) * F + f) * T.n_d1 * ZW;
-    const uint32_t *__restrict__ bits_prev =
-        Wp->bits + ((size_t)((t - 1) & 1) * F + f) * T.n_d1 * ZW;
-    const uint32_t *__restrict__ syn = Wp->syn + (size_t)f * Wp->words_m;
-    const bool soft = Wp->soft != 0;
-    float *__restrict__ post1 = soft ? Wp->post1 + ((size_t)(t & 1) * F + f) * T.n_d1 * Z : nullptr;
-    const float *__restrict__ llr = Wp->llr + (size_t)f * Wp->n;
+// ---- check-node pass
+//
+// Pass modes (uniform per launch): iteration 1 updates without reading old
+// messages; later iterations read them; the stop test of iteration t-1 runs
+// when t-1 >= et_start; the pass after the last iteration only tests.
+enum CnMode { kFirst = 0, kSteady = 1, kSteadyTest = 2, kTestOnly = 3 };
 
+// Rows with exactly NH heavy and ND degree-1 circulants, pass mode MODE.
+//
+// Phase 1 issues every load of the kCnVpt owned checks (offsets i0 + u *
+// kThreads) before any Phi evaluation, so a thread keeps all its edges in
+// flight at once. Lanes past the end of the row load from the padding and
+// never store.
+//
+// Phase 2, per check: the stop test of iteration t-1 (syndrome bit, heavy
+// posterior signs, degree-1 decisions of t-1); then L_vc = clip(L_v - m_cv),
+// Phi of every input, exclusive Phi sums by prefix/suffix (no subtraction,
+// so no cancellation), and signs as XOR of IEEE sign bits:
+//   sign(m_cv) = s_c xor (xor over all inputs) xor (own input).
+// Degree-1 neighbour p: C_p = [Q_p + m_cp < 0]; Phi is decreasing, so
+// |m_cp| > |Q_p| iff the exclusive sum is below Phi(|Q_p|).
+// Returns true if a check of iteration t-1 failed.
+template <int NH, int ND, int MODE>
+__device__ __forceinline__ bool cn_row(const Table &T, const Work &W, int f, int r, int t) {
+    constexpr int D = NH + ND;
+    constexpr int NHa = NH > 0 ? NH : 1;
+    constexpr int NDa = ND > 0 ? ND : 1;
+    constexpr bool kUpdate = MODE != kTestOnly;
+    constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
+    constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
+    constexpr int kWordStep = kThreads / 32;  // decision/syndrome words between owned checks
+    const int Z = T.Z, ZW = W.ZW;
+    const int rp = T.row_ptr[r];
+    const int lane = threadIdx.x & 31;
+    const int i0 = blockIdx.x * (kThreads * kCnVpt) + threadIdx.x;
+    const size_t bstride = (size_t)T.n_d1 * ZW;
+
+    // Per-edge pointers at this thread's first check; the other owned checks
+    // sit at fixed offsets (u * kThreads elements, u * kWordStep words).
+    const float *Lp[NHa];
+    float *Mp[NHa];
+    const float *Pp[NDa];
+    const uint32_t *Bp[NDa];
+    uint32_t *Bc[NDa];
+    {
+        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z + i0;
+        float *msg = W.msg + (size_t)f * T.n_h * Z + i0;
+        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z + i0;
+        const uint32_t *bprev =
+            W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride + (i0 >> 5);
+        uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride + (i0 >> 5);
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
+            if (k < NH) {
+                Lp[k] = L + oa;
+                Mp[k] = msg + ob;
+            } else {
+                Pp[k - NH] = phiq + oa;
+                Bp[k - NH] = bprev + ob;
+                Bc[k - NH] = bcur + ob;
+            }
+        }
+    }
+    const int c0 = r * Z + i0;  // check index of the first owned check
+    const uint32_t *Sp = W.syn + (size_t)f * W.words_m + (c0 >> 5);
+    const int ssh = 31 - (c0 & 31);  // moves s_c to bit 31
+    const int dsh = 31 - lane;       // moves a degree-1 decision bit to bit 31
+
+    // ---- phase 1: every load (lanes past the row read padding; the
+    // syndrome, a caller buffer, is read only for valid checks)
+    float lv[kCnVpt][NHa], mo[kCnVpt][NHa], pq[kCnVpt][NDa];
+    uint32_t sb[kCnVpt], par[kCnVpt];
+#pragma unroll
+    for (int u = 0; u < kCnVpt; u++) {
+        const bool valid = i0 + u * kThreads < Z;
+        sb[u] = valid ? (__ldg(Sp + u * kWordStep) << ssh) : 0u;
+        par[u] = 0;
+#pragma unroll
+        for (int k = 0; k < NH; k++) {
+            lv[u][k] = Lp[k][u * kThreads];
+            mo[u][k] = kReadMsg ? Mp[k][u * kThreads] : 0.0f;
+        }
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            pq[u][k] = kUpdate ? __ldg(Pp[k] + u * kThreads) : 0.0f;
+            if (kTest) par[u] ^= __ldg(Bp[k] + u * kWordStep) << dsh;
+        }
+    }
+
+    // ---- phase 2
     bool bad = false;
-#pragma unroll 1
+#pragma unroll
     for (int u = 0; u < kCnVpt; u++) {
         const int i = i0 + u * kThreads;
         const bool valid = i < Z;
-        float phi[MAXD];
-        uint32_t neg = 0;   // bit k: incoming L_vc of edge k is negative
-        uint32_t sbit = 0;  // syndrome bit of this check
-        uint32_t par = 0;   // parity of iteration t-1's decisions
+        if (kTest) {
+            uint32_t p = sb[u] ^ par[u];
 #pragma unroll
-        for (int k = 0; k < MAXD; k++) phi[k] = 0.0f;
-        if (valid) {
-            const int64_t c = (int64_t)r * Z + i;
-            sbit = (__ldg(syn + (c >> 5)) >> (c & 31)) & 1u;
+            for (int k = 0; k < NH; k++) p ^= fbits(lv[u][k]);
+            bad |= valid && (p & kSign) != 0;
+        }
+        if (!kUpdate) continue;
+        float phi[D];
+        uint32_t sg[D];
+        uint32_t stot = sb[u];
 #pragma unroll
-            for (int k = 0; k < MAXD; k++) {
-                if (k >= deg) break;
-                const qc::RowEnt e = T.rows[rp + k];
-                if (k < nh) {
+        for (int k = 0; k < NH; k++) {
+            const float d = lv[u][k] - mo[u][k];
+            phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
+            sg[k] = fbits(d);
+            stot ^= sg[k];
+        }
+#pragma unroll
+        for (int k = 0; k < ND; k++) {
+            phi[NH + k] = fabsf(pq[u][k]);
+            sg[NH + k] = fbits(pq[u][k]);
+            stot ^= sg[NH + k];
+        }
+        float pre[D + 1], suf[D + 1];
+        pre[0] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < D; k++) pre[k + 1] = pre[k] + phi[k];
+        suf[D] = 0.0f;
+#pragma unroll
+        for (int k = D - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
+            const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
+            if (k < NH) {
+                const float mag = fminf(psi_f(ex), W.clip);
+                if (valid) Mp[k][u * kThreads] = __uint_as_float(fbits(mag) ^ sk);
+            } else {
+                const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
+                const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
+                if (lane == 0 && valid) Bc[k - NH][u * kWordStep] = word;
+                if (W.soft && valid) {
+                    const qc::RowEnt e = T.rows[rp + k];
                     int vo = i + e.shift;
                     if (vo >= Z) vo -= Z;
-                    const float lv = L[(size_t)e.slot * Z + vo];
-                    par ^= lv < 0.0f ? 1u : 0u;
-                    if (update) {
-                        const float mo = t > 1 ? msg[(size_t)e.id * Z + i] : 0.0f;
-                        const float lvc = clampf(lv - mo, clip);
-                        phi[k] = phi_f(fmaxf(fabsf(lvc), xmin));
-                        neg |= (lvc < 0.0f ? 1u : 0u) << k;
-                    }
-                } else {
-                    par ^= (__ldg(bits_prev + (size_t)e.id * ZW + (i >> 5)) >> (i & 31)) & 1u;
-                    if (update) {
-                        const float p = __ldg(phiq + (size_t)e.id * Z + i);
-                        phi[k] = fabsf(p);
-                        neg |= (p < 0.0f ? 1u : 0u) << k;
-                    }
-                }
-            }
-            if (check && ((par ^ sbit) & 1u)) bad = true;
-        }
-        if (update) {
-            // exclusive Phi sums by prefix/suffix (no subtraction: no cancellation)
-            float pre[MAXD + 1], suf[MAXD + 1];
-            pre[0] = 0.0f;
-#pragma unroll
-            for (int k = 0; k < MAXD; k++) pre[k + 1] = pre[k] + phi[k];
-            suf[MAXD] = 0.0f;
-#pragma unroll
-            for (int k = MAXD - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
-            const uint32_t sgn_all = (sbit + __popc(neg)) & 1u;
-#pragma unroll
-            for (int k = 0; k < MAXD; k++) {
-                if (k >= deg) break;
-                const qc::RowEnt e = T.rows[rp + k];
-                const float ex = fmaxf(pre[k] + suf[k + 1], xmin);
-                const uint32_t negk = sgn_all ^ ((neg >> k) & 1u);  // sign of m_cv
-                if (k < nh) {
-                    if (valid) {
-                        const float mag = fminf(phi_f(ex), clip);
-                        msg[(size_t)e.id * Z + i] = negk ? -mag : mag;
-                    }
-                } else {
-                    // degree-1 neighbour p: C_p = [Q_p + m_cp < 0]. Phi is
-                    // decreasing, so |m_cp| > |Q_p| iff ex < Phi(|Q_p|) = phi[k].
-                    const uint32_t qneg = (neg >> k) & 1u;
-                    const bool dec = valid && ((ex < phi[k]) ? negk : qneg);
-                    const uint32_t word = __ballot_sync(0xffffffffu, dec);
-                    if ((threadIdx.x & 31) == 0 && valid)
-                        bits_cur[(size_t)e.id * ZW + (i >> 5)] = word;
-                    if (soft && valid) {
-                        int vo = i + e.shift;
-                        if (vo >= Z) vo -= Z;
-                        const float mag = fminf(phi_f(ex), clip);
-                        post1[(size_t)e.id * Z + i] =
-                            llr[(size_t)e.col * Z + vo] + (negk ? -mag : mag);
-                    }
+                    const float mag = fminf(psi_f(ex), W.clip);
+                    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
+                    post1[T.row_off_a[rp + k] + i] =
+                        W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
+                        kLn2 * __uint_as_float(fbits(mag) ^ sk);
                 }
             }
         }
     }
-    if (check) {
-        if (__syncthreads_or(bad) && threadIdx.x == 0) Wp->fail[f] = 1;
+    return bad;
+}
+
+// Any row shape up to MAXD circulants (heavy first), runtime degree with
+// predication; used for shapes the exact instantiations do not cover.
+template <int MAXD>
+__device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, int f, int r, int t,
+                                               int mode) {
+    const bool update = mode != kTestOnly;
+    const bool read_msg = mode == kSteady || mode == kSteadyTest;
+    const bool test = mode == kSteadyTest || mode == kTestOnly;
+    const int Z = T.Z, ZW = W.ZW;
+    const int rp = T.row_ptr[r];
+    const int deg = T.row_ptr[r + 1] - rp;
+    const int nh = T.row_nh[r];
+    const int i0 = blockIdx.x * (kThreads * kCnVpt) + threadIdx.x;
+    float *msg = W.msg + (size_t)f * T.n_h * Z;
+    const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
+    const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
+    const size_t bstride = (size_t)T.n_d1 * ZW;
+    uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
+    const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
+    const uint32_t *syn = W.syn + (size_t)f * W.words_m;
+    bool bad = false;
+    for (int u = 0; u < kCnVpt; u++) {
+        const int i = i0 + u * kThreads;
+        const bool valid = i < Z;
+        const int cidx = r * Z + i;
+        const uint32_t sbit = __ldg(syn + min(cidx >> 5, (int)W.words_m - 1)) << (31 - (cidx & 31));
+        float phi[MAXD];
+        uint32_t sg[MAXD];
+        uint32_t stot = sbit, par = sbit;
+#pragma unroll
+        for (int k = 0; k < MAXD; k++) {
+            phi[k] = 0.0f;
+            sg[k] = 0;
+            if (k < deg) {
+                const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
+                if (k < nh) {
+                    const float lv = L[oa + i];
+                    par ^= fbits(lv);
+                    const float d = lv - (read_msg ? msg[ob + i] : 0.0f);
+                    phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
+                    sg[k] = fbits(d);
+                } else {
+                    const float p = update ? __ldg(phiq + oa + i) : 0.0f;
+                    if (test) par ^= __ldg(bprev + ob + (i >> 5)) << (31 - (i & 31));
+                    phi[k] = fabsf(p);
+                    sg[k] = fbits(p);
+                }
+                stot ^= sg[k];
+            }
+        }
+        if (test) bad |= valid && (par & kSign) != 0;
+        if (!update) continue;
+        float pre[MAXD + 1], suf[MAXD + 1];
+        pre[0] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < MAXD; k++) pre[k + 1] = pre[k] + phi[k];
+        suf[MAXD] = 0.0f;
+#pragma unroll
+        for (int k = MAXD - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
+#pragma unroll
+        for (int k = 0; k < MAXD; k++) {
+            if (k >= deg) break;
+            const qc::RowEnt e = T.rows[rp + k];
+            const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
+            const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
+            const uint32_t sk = (stot ^ sg[k]) & kSign;
+            if (k < nh) {
+                const float mag = fminf(psi_f(ex), W.clip);
+                if (valid) msg[ob + i] = __uint_as_float(fbits(mag) ^ sk);
+            } else {
+                const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
+                const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
+                if ((threadIdx.x & 31) == 0 && valid) bcur[ob + (i >> 5)] = word;
+                if (W.soft && valid) {
+                    int vo = i + e.shift;
+                    if (vo >= Z) vo -= Z;
+                    const float mag = fminf(psi_f(ex), W.clip);
+                    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
+                    post1[oa + i] = W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
+                                    kLn2 * __uint_as_float(fbits(mag) ^ sk);
+                }
+            }
+        }
+    }
+    return bad;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool cn_dispatch(const Table &T, const Work &W, int f, int r, int t,
+                                            int nh, int nd) {
+    switch (nh * 4 + nd) {
+        case 1 * 4 + 1: return cn_row<1, 1, MODE>(T, W, f, r, t);
+        case 2 * 4 + 0: return cn_row<2, 0, MODE>(T, W, f, r, t);
+        case 2 * 4 + 1: return cn_row<2, 1, MODE>(T, W, f, r, t);
+        case 3 * 4 + 0: return cn_row<3, 0, MODE>(T, W, f, r, t);
+        case 3 * 4 + 1: return cn_row<3, 1, MODE>(T, W, f, r, t);
+        case 4 * 4 + 0: return cn_row<4, 0, MODE>(T, W, f, r, t);
+        case 4 * 4 + 1: return cn_row<4, 1, MODE>(T, W, f, r, t);
+        default: return false;  // not reached: the caller routes other shapes to the fallback
+    }
+}
+
+__host__ __device__ constexpr bool exact_shape(int nh, int nd) {
+    return (nd == 1 && nh >= 1 && nh <= 4) || (nd == 0 && nh >= 2 && nh <= 4);
+}
+
+// Check-node pass of iteration t (see the file comment). Grid (tile, base
+// row, frame); one block covers kThreads * kCnVpt consecutive checks of one
+// row of one frame. The row shape and pass mode select an exactly unrolled
+// body (block-uniform switch); MAXD bounds the fallback for other shapes.
+template <int MAXD>
+__global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const __grid_constant__ Table T,
+                                                         const __grid_constant__ Work W) {
+    const int f = blockIdx.z;
+    if (W.active[f] == 0) return;  // block-uniform
+    const int r = blockIdx.y;
+    const int t = *W.t;
+    const int mode = t > W.max_iter ? kTestOnly
+                     : t == 1       ? kFirst
+                     : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
+    const int nh = T.row_nh[r];
+    const int nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
+    bool bad;
+    if (exact_shape(nh, nd)) {
+        switch (mode) {
+            case kFirst: bad = cn_dispatch<kFirst>(T, W, f, r, t, nh, nd); break;
+            case kSteady: bad = cn_dispatch<kSteady>(T, W, f, r, t, nh, nd); break;
+            case kSteadyTest: bad = cn_dispatch<kSteadyTest>(T, W, f, r, t, nh, nd); break;
+            default: bad = cn_dispatch<kTestOnly>(T, W, f, r, t, nh, nd); break;
+        }
+    } else {
+        bad = cn_row_generic<MAXD>(T, W, f, r, t, mode);
+    }
+    if (mode == kSteadyTest || mode == kTestOnly) {
+        if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;
     }
 }
 
 // Loop control, one block: apply the stop test of iteration t-1, count t up,
 // and keep the WHILE node running while any frame is active.
-__global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const Work *__restrict__ Wp,
+template <bool kInGraph>
+__global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constant__ Work W,
                                                             cudaGraphConditionalHandle handle) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    const Work W = *Wp;
     const int t = *W.t;
     const bool last = t == W.max_iter + 1;
     const bool checked = last || (t >= 2 && t - 1 >= W.et_start);
@@ -320,53 +528,56 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const Work *__restri
     __syncthreads();
     if (threadIdx.x == 0) {
         *W.t = t + 1;
-        cudaGraphSetConditional(handle, any ? 1u : 0u);
+        if (kInGraph) cudaGraphSetConditional(handle, any ? 1u : 0u);
     }
 }
 
 // Variable-node pass: L_v = Q_v + sum_c m_cv for every heavy variable node.
+// Grid (tile, heavy column, frame). Lanes past the end of the column read
+// message padding (never stored); the channel LLRs, the caller's buffer, are
+// read only in range.
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
-                                                      const Work *__restrict__ Wp) {
-    const int f = blockIdx.y;
-    if (Wp->active[f] == 0) return;
+                                                      const __grid_constant__ Work W) {
+    const int f = blockIdx.z;
+    if (W.active[f] == 0) return;
     const int Z = T.Z;
-    const int span = kThreads * kVnVpt;
-    const int tiles = (Z + span - 1) / span;
-    const int hc = blockIdx.x / tiles;
-    const int j0 = (blockIdx.x - hc * tiles) * span + threadIdx.x;
-    const float *__restrict__ msg = Wp->msg + (size_t)f * T.n_h * Z;
-    const float *__restrict__ q = Wp->llr + (size_t)f * Wp->n + (size_t)T.hcol_base[hc] * Z;
-    float *__restrict__ L = Wp->L + ((size_t)f * T.n_hcols + hc) * Z;
+    const int hc = blockIdx.y;
+    const int j0 = blockIdx.x * (kThreads * kVnVpt) + threadIdx.x;
+    const float *__restrict__ msg = W.msg + (size_t)f * T.n_h * Z;
+    const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
+    float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
     float acc[kVnVpt];
 #pragma unroll
     for (int u = 0; u < kVnVpt; u++) {
         const int j = j0 + u * kThreads;
-        acc[u] = j < Z ? __ldg(q + j) : 0.0f;
+        acc[u] = j < Z ? __ldg(q + j) * kLog2e : 0.0f;
     }
     const int ce = T.col_ptr[hc + 1];
-#pragma unroll 4
+#pragma unroll kVnUnroll
     for (int k = T.col_ptr[hc]; k < ce; k++) {
         const qc::ColEnt e = T.cols[k];
-        const float *__restrict__ mk = msg + (size_t)e.id * Z;
+        const float *__restrict__ mk = msg + e.id * Z;
 #pragma unroll
         for (int u = 0; u < kVnVpt; u++) {
-            const int j = j0 + u * kThreads;
-            int idx = j - e.shift;
+            int idx = j0 + u * kThreads - e.shift;
             if (idx < 0) idx += Z;
-            if (j < Z) acc[u] += mk[idx];
+            acc[u] += mk[idx];
         }
     }
 #pragma unroll
     for (int u = 0; u < kVnVpt; u++) {
         const int j = j0 + u * kThreads;
-        if (j < Z) L[j] = acc[u];
+        if (j < Z) {
+            const float lvj = acc[u] + 0.0f;  // -0 -> +0: sgn(0) = +1 everywhere
+            L[j] = lvj;
+            L[j + Z] = lvj;
+        }
     }
 }
 
 // Outputs: packed key bits C_v (v < k) and, for soft output, every posterior.
 __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__ Table T,
-                                                         const Work *__restrict__ Wp) {
-    const Work W = *Wp;
+                                                         const __grid_constant__ Work W) {
     const int Z = T.Z;
     const int lane = threadIdx.x & 31;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,7 +593,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__
             const int c = (int)(v / Z), j = (int)(v - (int64_t)c * Z);
             const int kind = T.col_kind[c];
             if (kind >= 0) {
-                dec = W.L[((size_t)f * T.n_hcols + kind) * Z + j] < 0.0f;
+                dec = W.L[((size_t)f * T.n_hcols + kind) * 2 * Z + j] < 0.0f;
             } else {
                 const int d = -kind - 2;
                 int i = j - T.d1_shift[d];
@@ -405,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__
             const int kind = T.col_kind[c];
             float val;
             if (kind >= 0) {
-                val = W.L[((size_t)f * T.n_hcols + kind) * Z + j];
+                val = W.L[((size_t)f * T.n_hcols + kind) * 2 * Z + j] * kLn2;
             } else {
                 const int d = -kind - 2;
                 int i = j - T.d1_shift[d];
@@ -418,10 +629,18 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__
     }
 }
 
+// Measurement support: put the decoder back into a mid-loop state (t = 2,
+// every frame active) so that a replayed check-node pass does a full update.
+__global__ void replay_prep_kernel(const __grid_constant__ Work W) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) *W.t = 2;
+    for (int f = tid; f < W.n_frames; f += gridDim.x * blockDim.x) W.active[f] = 1;
+}
+
 // ------------------------------------------------------------ host side
 
 struct Layout {
-    size_t work, t, active, fail, msg, L, phiq, bits, post1, total;
+    size_t t, active, fail, msg, L, phiq, bits, post1, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -435,44 +654,26 @@ Layout layout_of(const Table &T, int F, bool soft) {
         return at;
     };
     const size_t Z = (size_t)T.Z, ZW = (Z + 31) / 32;
-    o.work = take(sizeof(Work));
     o.t = take(sizeof(int32_t));
     o.active = take(sizeof(int32_t) * F);
     o.fail = take(sizeof(int32_t) * F);
-    o.msg = take(sizeof(float) * F * T.n_h * Z);
-    o.L = take(sizeof(float) * F * T.n_hcols * Z);
-    o.phiq = take(sizeof(float) * F * T.n_d1 * Z);
-    o.bits = take(sizeof(uint32_t) * 2 * F * T.n_d1 * ZW);
-    o.post1 = soft ? take(sizeof(float) * 2 * F * T.n_d1 * Z) : 0;
+    o.msg = take(sizeof(float) * (F * T.n_h * Z + kSlack));
+    o.L = take(sizeof(float) * (F * T.n_hcols * 2 * Z + kSlack));
+    o.phiq = take(sizeof(float) * (F * T.n_d1 * Z + kSlack));
+    o.bits = take(sizeof(uint32_t) * (2 * F * T.n_d1 * ZW + kSlack));
+    o.post1 = soft ? take(sizeof(float) * (2 * F * T.n_d1 * Z + kSlack)) : 0;
     o.total = off;
     return o;
 }
 
-struct GraphCache {
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t args_node = nullptr;
-    void *ws = nullptr;
-    int n_frames = 0;
-    int soft = 0;
-};
-
-void free_cache(GraphCache *gc) {
-    if (!gc) return;
-    if (gc->exec) cudaGraphExecDestroy(gc->exec);
-    if (gc->graph) cudaGraphDestroy(gc->graph);
-    gc->exec = nullptr;
-    gc->graph = nullptr;
-}
-
-int cn_blocks_x(const Table &T) {
+dim3 cn_grid(const Table &T, int F) {
     const int span = kThreads * kCnVpt;
-    return T.mb * ((T.Z + span - 1) / span);
+    return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)T.mb, (unsigned)F);
 }
 
-int vn_blocks_x(const Table &T) {
+dim3 vn_grid(const Table &T, int F) {
     const int span = kThreads * kVnVpt;
-    return T.n_hcols * ((T.Z + span - 1) / span);
+    return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)std::max(T.n_hcols, 1), (unsigned)F);
 }
 
 int sm_count() {
@@ -483,9 +684,28 @@ int sm_count() {
 }
 
 void *cn_kernel_for(int maxdeg) {
-    if (maxdeg <= 4) return (void *)cn_kernel<4>;
+    if (maxdeg <= 5) return (void *)cn_kernel<5>;
     if (maxdeg <= 8) return (void *)cn_kernel<8>;
     return (void *)cn_kernel<16>;
+}
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    Work key;
+    unsigned long long stamp = 0;
+};
+
+struct GraphCache {
+    GraphEntry e[kGraphCacheSize];
+    unsigned long long clock = 0;
+};
+
+void free_entry(GraphEntry &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
 }
 
 cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep,
@@ -500,31 +720,22 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
 }
 
-// Build and instantiate the decode graph for (code, frames, workspace).
-int build_graph(const qcldpc_code *code, GraphCache *gc, int F, void *ws, bool soft,
-                const Work &w0) {
+// Build and instantiate the decode graph for one argument set.
+int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
     const Table &T = code->tab;
-    const Layout lo = layout_of(T, F, soft);
-    Work *dwork = reinterpret_cast<Work *>(static_cast<char *>(ws) + lo.work);
+    const int F = w0.n_frames;
     cudaError_t err;
     cudaGraph_t g = nullptr;
     if ((err = cudaGraphCreate(&g, 0)) != cudaSuccess) return qc::cuda_fail(err, "decode: cudaGraphCreate");
-    gc->graph = g;
-
-    Work wcopy = w0;
-    void *args_args[] = {&wcopy, &dwork};
-    cudaGraphNode_t n_args, n_init, n_cond, n_final;
-    if ((err = add_kernel(&n_args, g, nullptr, 0, (void *)args_kernel, dim3(1), dim3(32),
-                          args_args)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode: add args node");
-
+    ge.graph = g;
     Table tcopy = T;
-    void *tab_args[] = {&tcopy, &dwork};
-    const int init_blocks = sm_count() * 4;
-    if ((err = add_kernel(&n_init, g, &n_args, 1, (void *)init_kernel, dim3(init_blocks),
-                          dim3(kThreads), tab_args)) != cudaSuccess)
+    Work wcopy = w0;
+    void *args[] = {&tcopy, &wcopy};
+    const int blocks = sm_count() * 4;
+    cudaGraphNode_t n_init, n_cond, n_final;
+    if ((err = add_kernel(&n_init, g, nullptr, 0, (void *)init_kernel, dim3(blocks), dim3(kThreads),
+                          args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add init node");
-
     cudaGraphConditionalHandle handle;
     if ((err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault)) !=
         cudaSuccess)
@@ -537,31 +748,54 @@ int build_graph(const qcldpc_code *code, GraphCache *gc, int F, void *ws, bool s
     if ((err = cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add conditional node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-
     cudaGraphNode_t n_cn, n_ctrl, n_vn;
-    if ((err = add_kernel(&n_cn, body, nullptr, 0, cn_kernel_for(T.max_row_deg),
-                          dim3(cn_blocks_x(T), F), dim3(kThreads), tab_args)) != cudaSuccess)
+    if ((err = add_kernel(&n_cn, body, nullptr, 0, cn_kernel_for(T.max_row_deg), cn_grid(T, F),
+                          dim3(kThreads), args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add check-node kernel");
-    void *ctrl_args[] = {&dwork, &handle};
-    if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel, dim3(1),
+    void *ctrl_args[] = {&wcopy, &handle};
+    if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                           dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add control kernel");
-    if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, (void *)vn_kernel, dim3(vn_blocks_x(T), F),
-                          dim3(kThreads), tab_args)) != cudaSuccess)
+    if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, (void *)vn_kernel, vn_grid(T, F), dim3(kThreads),
+                          args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add variable-node kernel");
-
-    if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(init_blocks),
-                          dim3(kThreads), tab_args)) != cudaSuccess)
+    if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks),
+                          dim3(kThreads), args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add output kernel");
-
     cudaGraphExec_t exec = nullptr;
     if ((err = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: cudaGraphInstantiate");
-    gc->exec = exec;
-    gc->args_node = n_args;
-    gc->ws = ws;
-    gc->n_frames = F;
-    gc->soft = soft ? 1 : 0;
+    ge.exec = exec;
+    ge.key = w0;
+    return QCLDPC_OK;
+}
+
+// launch_mode 1: the same passes as the graph, enqueued one by one.
+int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
+    const Table &T = code->tab;
+    const int F = w.n_frames;
+    const int blocks = sm_count() * 4;
+    init_kernel<<<blocks, kThreads, 0, stream>>>(T, w);
+    void *cn = cn_kernel_for(T.max_row_deg);
+    Table tcopy = T;
+    Work wcopy = w;
+    void *args[] = {&tcopy, &wcopy};
+    cudaGraphConditionalHandle none = 0;
+    cudaError_t err = cudaGetLastError();
+    for (int t = 1; t <= w.max_iter + 1 && err == cudaSuccess; t++) {
+        err = cudaLaunchKernel(cn, cn_grid(T, F), dim3(kThreads), args, 0, stream);
+        if (err != cudaSuccess) break;
+        ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
+        if (t <= w.max_iter)
+            err = cudaLaunchKernel((void *)vn_kernel, vn_grid(T, F), dim3(kThreads), args, 0, stream);
+        if (err == cudaSuccess) err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) {
+        final_kernel<<<blocks, kThreads, 0, stream>>>(T, w);
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) return qc::cuda_fail(err, "decode (stream mode): launch");
+    qc::clear_error();
     return QCLDPC_OK;
 }
 
@@ -577,8 +811,8 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     const bool soft = post != nullptr;
     if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode: n_frames must be in [0, 65535]");
     if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
-    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format != 0 || p.reserved[0] ||
-        p.reserved[1])
+    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format != 0 || p.reserved ||
+        (p.launch_mode != 0 && p.launch_mode != 1))
         return fail(QCLDPC_E_INVAL, "decode: unsupported option (phi_floor > 0, flooding, FP32)");
     if (soft && p.soft_output != 1)
         return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
@@ -599,6 +833,7 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
     char *base = static_cast<char *>(ws);
     Work w;
+    std::memset(&w, 0, sizeof(w));  // padding bytes take part in cache keys
     w.llr = llr;
     w.syn = syn;
     w.keys = keys;
@@ -621,51 +856,41 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.et_start = p.et_start;
     w.soft = soft ? 1 : 0;
     w.ZW = (T.Z + 31) / 32;
-    w.clip = p.clip > 0.0f ? p.clip : INFINITY;
-    w.xmin = p.phi_floor;
+    w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;  // base-2 units
+    w.xmin = p.phi_floor * kLog2e;
 
     std::lock_guard<std::mutex> lock(code->mu);
+    code->last_ws = ws;
+    code->last_frames = F;
+    code->last_soft = soft ? 1 : 0;
+    std::memcpy(code->last_work, &w, sizeof(w));
+    if (p.launch_mode == 1) return stream_decode(code, w, stream);
+
     GraphCache *gc = static_cast<GraphCache *>(code->graph_cache);
     if (!gc) {
         gc = new (std::nothrow) GraphCache();
         if (!gc) return fail(QCLDPC_E_NOMEM, "decode: out of host memory");
         code->graph_cache = gc;
     }
-    if (!gc->exec || gc->ws != ws || gc->n_frames != F || gc->soft != (soft ? 1 : 0)) {
-        free_cache(gc);
-        int st = build_graph(code, gc, F, ws, soft, w);
+    GraphEntry *hit = nullptr, *victim = &gc->e[0];
+    for (auto &e : gc->e) {
+        if (e.exec && std::memcmp(&e.key, &w, sizeof(w)) == 0) hit = &e;
+        if (!e.exec || (victim->exec && e.stamp < victim->stamp)) victim = &e;
+    }
+    if (!hit) {
+        free_entry(*victim);
+        int st = build_graph(code, *victim, w);
         if (st != QCLDPC_OK) {
-            free_cache(gc);
+            free_entry(*victim);
             return st;
         }
-    } else {
-        Layout l2 = layout_of(T, F, soft);
-        Work *dwork = reinterpret_cast<Work *>(base + l2.work);
-        void *args_args[] = {&w, &dwork};
-        cudaKernelNodeParams kp = {};
-        kp.func = (void *)args_kernel;
-        kp.gridDim = dim3(1);
-        kp.blockDim = dim3(32);
-        kp.kernelParams = args_args;
-        if ((err = cudaGraphExecKernelNodeSetParams(gc->exec, gc->args_node, &kp)) != cudaSuccess)
-            return cuda_fail(err, "decode: cudaGraphExecKernelNodeSetParams");
+        hit = victim;
     }
-    if ((err = cudaGraphLaunch(gc->exec, stream)) != cudaSuccess)
+    hit->stamp = ++gc->clock;
+    if ((err = cudaGraphLaunch(hit->exec, stream)) != cudaSuccess)
         return cuda_fail(err, "decode: cudaGraphLaunch");
     clear_error();
     return QCLDPC_OK;
-}
-
-// Measurement support: put the decoder back into a mid-loop state (t = 2,
-// every frame active, at least two iterations) so that a replayed check-node
-// pass does a full message update.
-__global__ void replay_prep_kernel(Work *Wp) {
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid == 0) {
-        *Wp->t = 2;
-        if (Wp->max_iter < 2) Wp->max_iter = 2;
-    }
-    for (int f = tid; f < Wp->n_frames; f += gridDim.x * blockDim.x) Wp->active[f] = 1;
 }
 
 }  // namespace
@@ -674,7 +899,7 @@ namespace qc {
 void destroy_graph_cache(qcldpc_code *code) {
     GraphCache *gc = static_cast<GraphCache *>(code->graph_cache);
     if (!gc) return;
-    free_cache(gc);
+    for (auto &e : gc->e) free_entry(e);
     delete gc;
     code->graph_cache = nullptr;
 }
@@ -718,40 +943,38 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
         n_frames > 65535)
         return fail(QCLDPC_E_INVAL, "time_passes: bad argument");
     cudaStream_t stream = (cudaStream_t)stream_;
-    {
-        std::lock_guard<std::mutex> lock(code->mu);
-        GraphCache *gc = static_cast<GraphCache *>(code->graph_cache);
-        if (!gc || !gc->exec || gc->ws != workspace_dev || gc->n_frames != n_frames)
-            return fail(QCLDPC_E_INVAL,
-                        "time_passes: no decode ran on this workspace with this frame count");
-        const Layout lo = layout_of(code->tab, n_frames, gc->soft != 0);
-        if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "time_passes: workspace too small");
-        Work *dwork = reinterpret_cast<Work *>(static_cast<char *>(workspace_dev) + lo.work);
-        cudaEvent_t ev[3];
-        cudaError_t err = cudaSuccess;
-        for (int i = 0; i < 3; i++)
-            if ((err = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(err, "time_passes: cudaEventCreate");
-        const Table &T = code->tab;
-        replay_prep_kernel<<<1, 256, 0, stream>>>(dwork);
-        void *cn = cn_kernel_for(T.max_row_deg);
-        void *args[] = {const_cast<Table *>(&T), &dwork};
-        cudaEventRecord(ev[0], stream);
-        for (int r = 0; r < reps && err == cudaSuccess; r++)
-            err = cudaLaunchKernel(cn, dim3(cn_blocks_x(T), n_frames), dim3(kThreads), args, 0, stream);
-        cudaEventRecord(ev[1], stream);
-        for (int r = 0; r < reps && err == cudaSuccess; r++)
-            err = cudaLaunchKernel((void *)vn_kernel, dim3(vn_blocks_x(T), n_frames), dim3(kThreads),
-                                   args, 0, stream);
-        cudaEventRecord(ev[2], stream);
-        if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
-        float a = 0.f, b = 0.f;
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&a, ev[0], ev[1]);
-        if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[1], ev[2]);
-        for (int i = 0; i < 3; i++) cudaEventDestroy(ev[i]);
-        if (err != cudaSuccess) return cuda_fail(err, "time_passes");
-        *cn_ms = a / reps;
-        *vn_ms = b / reps;
-    }
+    std::lock_guard<std::mutex> lock(code->mu);
+    if (code->last_ws != workspace_dev || code->last_frames != n_frames)
+        return fail(QCLDPC_E_INVAL, "time_passes: no decode ran on this workspace with this frame count");
+    const Layout lo = layout_of(code->tab, n_frames, code->last_soft != 0);
+    if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "time_passes: workspace too small");
+    Work w;
+    std::memcpy(&w, code->last_work, sizeof(w));
+    if (w.max_iter < 2) w.max_iter = 2;  // replays run as iteration 2: a full update
+    cudaEvent_t ev[3];
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < 3; i++)
+        if ((err = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(err, "time_passes: cudaEventCreate");
+    const Table &T = code->tab;
+    replay_prep_kernel<<<1, 256, 0, stream>>>(w);
+    void *cn = cn_kernel_for(T.max_row_deg);
+    Table tcopy = T;
+    void *args[] = {&tcopy, &w};
+    cudaEventRecord(ev[0], stream);
+    for (int r = 0; r < reps && err == cudaSuccess; r++)
+        err = cudaLaunchKernel(cn, cn_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+    cudaEventRecord(ev[1], stream);
+    for (int r = 0; r < reps && err == cudaSuccess; r++)
+        err = cudaLaunchKernel((void *)vn_kernel, vn_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+    cudaEventRecord(ev[2], stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
+    float a = 0.f, b = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&a, ev[0], ev[1]);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[1], ev[2]);
+    for (int i = 0; i < 3; i++) cudaEventDestroy(ev[i]);
+    if (err != cudaSuccess) return cuda_fail(err, "time_passes");
+    *cn_ms = a / reps;
+    *vn_ms = b / reps;
     clear_error();
     return QCLDPC_OK;
 }

@@ -51,6 +51,12 @@ struct Table {
     int16_t hcol_base[kMaxHeavyCols];   // base column of each heavy slot
     int16_t col_kind[kMaxCols];         // >= 0 heavy slot; <= -2: d1 id = -kind-2
     RowEnt rows[kMaxCirc];
+    // Per row entry, in elements of one frame's arrays: heavy entries
+    // off_a = slot * 2Z + shift (posterior read), off_b = id * Z (messages);
+    // degree-1 entries off_a = id * Z (Phi values), off_b = id * ceil(Z/32)
+    // (decision words).
+    int32_t row_off_a[kMaxCirc];
+    int32_t row_off_b[kMaxCirc];
     ColEnt cols[kMaxCirc];
     int32_t d1_shift[kMaxCirc];
     int16_t d1_row[kMaxCirc];
@@ -65,6 +71,10 @@ struct qcldpc_code {
     int64_t n, m, k, n_edges;
     std::mutex mu;      // serialises decode calls on this handle
     void *graph_cache;  // decoder graph state (decode.cu), may be NULL
+    void *last_ws;      // workspace, frame count and soft flag of the last decode
+    int last_frames;
+    int last_soft;
+    unsigned char last_work[256];  // the last decode's kernel arguments (decode.cu)
 };
 
 namespace qc {

@@ -1,23 +1,33 @@
-"""Derive the FP32 polynomial pieces of Phi(x) = -ln tanh(x/2) used by the kernels.
+"""Derive the FP32 polynomial pieces of the check-node function used by the kernels.
 
-Phi is split at x = 1:
+The decoder keeps every LLR in base-2 units (y = x log2(e), x the natural
+LLR). In those units Phi(x) = -ln tanh(x/2) becomes
 
-* x <= 1:  Phi(x) = ln(2/x) + ln(u coth u), u = x/2. The second term is an
-  even function, written as w * G(w) with w = x^2 and G a cubic.
-* x > 1:   Phi(x) = 2 atanh(t), t = e^{-x} <= e^{-1}; 2 atanh(t) = 2 t A(t^2)
-  with A(v) = atanh(sqrt v)/sqrt v = 1 + v/3 + v^2/5 + ..., fitted by a quartic.
+    psi(y) = log2(e) Phi(y ln 2) = log2 coth(y ln2 / 2),
+
+and the check-node rule keeps its form: m2 = psi(sum psi(|L2|)). Working in
+base 2 lets the hardware ex2/lg2 take their arguments without scaling.
+psi is split at y = 1/ln2 (x = 1):
+
+* small y: psi(y) = C - log2(y) + w G(w), w = y^2, C = 1 - log2(ln 2); w G(w)
+  is log2(u coth u) with u = y ln2 / 2, an even function fitted by a cubic
+  in w;
+* large y: psi(y) = (2/ln 2) atanh(t), t = 2^-y, written t A(t^2) with
+  A(v) = (2/ln 2) atanh(sqrt v)/sqrt v, fitted by a quartic in v.
 
 The coefficients are near-minimax fits in relative error (Lawson reweighting
-of least squares on Chebyshev nodes) against high-precision references of the
-two series, computed with mpmath. Run ``python -m paper_1702_07740_gb300.phi_fit``
-to print them; the values in ``csrc/decode.cu`` come from this script.
-A development-time helper: the library never imports it.
+of least squares on Chebyshev nodes) against mpmath references of the two
+series. Run ``python -m paper_1702_07740_gb300.phi_fit`` to print them; the
+values in ``csrc/decode.cu`` come from this script. A development-time helper:
+the library never imports it.
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
-X_SPLIT = 1.0
+Y_SPLIT = 1.0 / math.log(2.0)
 
 
 def _fit(fun, lo, hi, deg, n=400, rounds=50):
@@ -39,26 +49,29 @@ def _fit(fun, lo, hi, deg, n=400, rounds=50):
 def coefficients():
     import mpmath as mpm
     mpm.mp.dps = 40
+    ln2 = mpm.log(2)
 
-    def g_over_w(w):
+    def g_over_w(w):  # log2(u coth u) / y^2, u = y ln2 / 2, w = y^2
         if w == 0:
-            return 1.0 / 12.0
-        u = mpm.sqrt(mpm.mpf(w)) / 2
-        return float(mpm.log(u * mpm.coth(u)) / w)
+            return float(ln2 ** 2 / 12 / ln2)  # limit: (u^2/3)/ln2 / y^2
+        u = mpm.sqrt(mpm.mpf(w)) * ln2 / 2
+        return float(mpm.log(u * mpm.coth(u)) / ln2 / w)
 
-    def a_of_v(v):
+    def a_of_v(v):  # (2/ln2) atanh(sqrt v)/sqrt v
         if v == 0:
-            return 1.0
+            return float(2 / ln2)
         r = mpm.sqrt(mpm.mpf(v))
-        return float(mpm.atanh(r) / r)
+        return float(2 / ln2 * mpm.atanh(r) / r)
 
-    G = _fit(g_over_w, 0.0, X_SPLIT ** 2, 3)
-    A = _fit(a_of_v, 0.0, float(mpm.e ** (-2 * X_SPLIT)), 4)
-    return np.float32(G), np.float32(A)
+    G = _fit(g_over_w, 0.0, Y_SPLIT ** 2, 3)
+    A = _fit(a_of_v, 0.0, float(mpm.power(2, -2 * Y_SPLIT)), 4)
+    C = float(1 - mpm.log(ln2, 2))
+    return np.float32(G), np.float32(A), np.float32(C)
 
 
 if __name__ == "__main__":
-    G, A = coefficients()
+    G, A, C = coefficients()
+    print(f"constexpr float kC = {C:.9e}f;")
     for name, arr in (("G", G), ("A", A)):
         for i, c in enumerate(arr):
             print(f"constexpr float k{name}{i} = {c:.9e}f;")

@@ -45,7 +45,8 @@ class qcldpc_params(ctypes.Structure):
         ("schedule", ctypes.c_int32),
         ("msg_format", ctypes.c_int32),
         ("soft_output", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("launch_mode", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -63,8 +64,8 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
-        if build_if_missing and not _build.up_to_date():
+        path = os.environ.get("QCLDPC_LIB") or _build.LIB
+        if path == _build.LIB and build_if_missing and not _build.up_to_date():
             path = _build.build()
         if not os.path.exists(path):
             raise RuntimeError(f"libqcldpc.so not built ({path}); run __graft_entry__.build()")

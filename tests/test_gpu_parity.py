@@ -262,6 +262,17 @@ def test_decode_is_deterministic():
         np.testing.assert_array_equal(o[0], outs[0][0])
 
 
+def test_stream_launch_mode_matches_graph_mode():
+    """launch_mode 1 (host-enqueued passes) computes exactly what the graph does."""
+    fr = make_frames(synth.rate002_code(64), 0.08, 6)
+    code = q.create_code_from(fr.code_dict)
+    llr = gpu_llr(fr)
+    a = decode_soft(code, llr, fr.syn, fr.F, 40)
+    b = decode_soft(code, llr, fr.syn, fr.F, 40, launch_mode=1)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+
+
 def test_decode_zero_frames_and_bad_args():
     code = q.create_code_from(synth.rate002_code(64))
     dec = q.Decoder(code, 1)
@@ -302,12 +313,13 @@ def test_full_size_batch_parity_few_iterations():
 
 
 def test_full_size_converged_frames_satisfy_the_syndrome():
-    """At a higher SNR most n=10^6 frames converge: the hard decisions of every
-    converged frame satisfy H C = s (checked by the oracle's syndrome)."""
+    """At SNR 0.15 n=10^6 frames converge within a few iterations: the hard
+    decisions of every converged frame satisfy H C = s (checked by the
+    oracle's syndrome), and the key bits are those decisions."""
     F = 4
-    fr = make_frames(synth.rate002_code(20000), 0.08, F)
+    fr = make_frames(synth.rate002_code(20000), 0.15, F)
     code = q.create_code_from(fr.code_dict)
-    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, F, 100)
+    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, F, 60)
     assert conv.sum() >= 1
     for f in range(F):
         chat = (post[f] < 0).astype(np.uint8)
