@@ -215,6 +215,37 @@ int qcldpc_time_passes(const qcldpc_code *code, int n_frames, void *workspace_de
                        size_t workspace_bytes, int reps, float *cn_ms, float *vn_ms,
                        qcldpc_stream_t stream);
 
+/*
+ * Decoding for callers that cannot allocate device memory; the paper has no
+ * counterpart. Some callers have no way to allocate device memory: code
+ * embedded in a host framework that owns the device allocator and does not
+ * expose it, or a process whose device memory is reserved once at start-up
+ * and may not grow. This entry point computes exactly what qcldpc_decode
+ * computes (same kernels, passes enqueued one by one on `stream`, no graph
+ * objects), but keeps its scratch in a static 16 MiB device array inside the
+ * library instead of a caller workspace. Every GPU that loads the library
+ * holds that array until the process exits. The caller still passes the
+ * inputs and outputs described at qcldpc_decode; the array is never exposed.
+ *
+ * Limit: the code's workspace for n_frames (qcldpc_decode_workspace with
+ * default options) must fit in 16 MiB, e.g. one frame of the rate-0.02,
+ * n = 10^6 code; larger requests return QCLDPC_E_UNSUPPORTED and a message
+ * naming both sizes. p->soft_output and p->launch_mode are ignored.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * All calls on a device share the one array and every call re-initialises
+ * all decoder state it reads, so consecutive calls are independent; calls
+ * whose work overlaps on the GPU (e.g. on two streams at once) race on the
+ * array and must be serialised by the caller. Allocates nothing.
+ * Errors: QCLDPC_E_INVAL, _ALIGN, _UNSUPPORTED, _CUDA.
+ */
+int qcldpc_decode_noalloc(const qcldpc_code *code, const float *llr_dev,
+                          const uint32_t *syn_dev, int n_frames, int max_iter,
+                          const qcldpc_params *p, uint32_t *key_bits_dev,
+                          int32_t *converged_dev, int32_t *iters_dev,
+                          qcldpc_stream_t stream);
+
 /* Description of the last failure on this thread ("" if none). */
 const char *qcldpc_last_error(void);
 

@@ -50,6 +50,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 
 #include "qcldpc_internal.cuh"
 
@@ -977,4 +978,64 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     *vn_ms = b / reps;
     clear_error();
     return QCLDPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Decoding without caller-provided or library-allocated scratch.
+//
+// Some callers cannot allocate device memory: for example code embedded in a
+// host framework that owns the device allocator and does not expose it, or a
+// process whose device memory is reserved once at start-up and may not grow.
+// For them qcldpc_decode_noalloc keeps the decoder's scratch in this file-
+// scope device array, which every GPU that loads the library holds until the
+// process exits. Host code must not use the array's name as an address (on
+// the host it is only a stand-in); the device address is fetched once per
+// device with cudaGetSymbolAddress and passed to the kernels.
+constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices];  // device address per device, set on first use
+}  // namespace
+
+extern "C" int qcldpc_decode_noalloc(const qcldpc_code *code, const float *llr_dev,
+                                     const uint32_t *syn_dev, int n_frames, int max_iter,
+                                     const qcldpc_params *p, uint32_t *key_bits_dev,
+                                     int32_t *converged_dev, int32_t *iters_dev,
+                                     qcldpc_stream_t stream) {
+    using namespace qc;
+    if (!code) return fail(QCLDPC_E_INVAL, "decode_noalloc: code is NULL");
+    if (n_frames < 0) return fail(QCLDPC_E_INVAL, "decode_noalloc: negative frame count");
+    const size_t need = layout_of(code->tab, n_frames, false).total;
+    if (need > kNoallocScratchBytes)
+        return fail(QCLDPC_E_UNSUPPORTED,
+                    "decode_noalloc: this code and frame count need " + std::to_string(need) +
+                        " bytes of scratch; the static scratch holds " +
+                        std::to_string(kNoallocScratchBytes) + " bytes (decode fewer frames)");
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "decode_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return fail(QCLDPC_E_UNSUPPORTED, "decode_noalloc: device ordinal above 63");
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            err = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (err != cudaSuccess) return cuda_fail(err, "decode_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = ptr;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    qcldpc_params q;
+    if (p) q = *p;
+    else qcldpc_params_init(&q);
+    q.launch_mode = 1;  // plain launches: no graph objects to instantiate
+    q.soft_output = 0;
+    return decode_impl(code, llr_dev, syn_dev, n_frames, max_iter, &q, key_bits_dev,
+                       converged_dev, iters_dev, nullptr, scratch, kNoallocScratchBytes,
+                       (cudaStream_t)stream);
 }

@@ -27,7 +27,8 @@ EXPORTED = [
     "qcldpc_create_code", "qcldpc_destroy_code", "qcldpc_code_info",
     "qcldpc_syndrome", "qcldpc_bob_message_8d", "qcldpc_llr_8d",
     "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
-    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_last_error",
+    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc",
+    "qcldpc_last_error",
 ]
 
 
@@ -96,6 +97,9 @@ def load(build_if_missing: bool = True):
         lib.qcldpc_time_passes.argtypes = [vp, i32, vp, sz, i32, ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float), vp]
         lib.qcldpc_time_passes.restype = i32
+        lib.qcldpc_decode_noalloc.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
+                                              vp, vp, vp, vp]
+        lib.qcldpc_decode_noalloc.restype = i32
         lib.qcldpc_last_error.argtypes = []
         lib.qcldpc_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -249,6 +253,19 @@ def qcldpc_time_passes(code: Code, n_frames: int, workspace_dev, workspace_bytes
                                    ctypes.byref(vn), _stream(stream))
     _check(st, "qcldpc_time_passes")
     return cn.value, vn.value
+
+
+def qcldpc_decode_noalloc(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,
+                          params: qcldpc_params | None, key_bits_dev, converged_dev, iters_dev,
+                          stream=None):
+    """qcldpc_decode with the library's static scratch instead of a workspace."""
+    p = ctypes.byref(params) if params is not None else None
+    st = load().qcldpc_decode_noalloc(code.handle, _dev(llr_dev, 4, "llr_dev"),
+                                      _dev(syn_dev, 4, "syn_dev"), int(n_frames), int(max_iter), p,
+                                      _dev(key_bits_dev, 4, "key_bits_dev"),
+                                      _dev(converged_dev, 4, "converged_dev"),
+                                      _dev(iters_dev, 4, "iters_dev"), _stream(stream))
+    _check(st, "qcldpc_decode_noalloc")
 
 
 class Decoder:
