@@ -134,7 +134,10 @@ typedef struct qcldpc_params {
                             iteration (delayed early termination, Sec. IV-A).
                             Default 1 */
     int32_t schedule;    /* 0 = flooding (the only schedule of this build) */
-    int32_t msg_format;  /* 0 = FP32 edge messages (the only format yet) */
+    int32_t msg_format;  /* storage of the check-to-variable messages, all
+                            arithmetic FP32: 0 = FP32 (default), 1 = FP16
+                            (round to nearest), 2 = int8 codes q with
+                            m = q * msg_step, |q| <= 127 (saturating) */
     int32_t soft_output; /* 1: reserve workspace for qcldpc_decode_soft */
     int32_t launch_mode; /* 0: the iteration loop runs inside one CUDA graph
                             (a conditional WHILE node; no host work per
@@ -143,7 +146,8 @@ typedef struct qcldpc_params {
                             the stream (passes after every frame stopped exit
                             at once); same results, meant for profilers that
                             cannot look inside conditional graphs. Default 0 */
-    int32_t reserved;    /* must be zero */
+    float msg_step;      /* int8 quantum in natural-LLR units; 0 (default)
+                            means clip / 127. Ignored for other formats */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);

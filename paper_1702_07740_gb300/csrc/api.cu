@@ -46,7 +46,7 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->msg_format = 0;
     p->soft_output = 0;
     p->launch_mode = 0;
-    p->reserved = 0;
+    p->msg_step = 0.0f;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,

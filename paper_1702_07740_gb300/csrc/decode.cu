@@ -49,8 +49,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+
+#include <cuda_fp16.h>
 
 #include "qcldpc_internal.cuh"
 
@@ -77,8 +80,24 @@ constexpr int kCnVpt = QCLDPC_CN_VPT;  // checks per thread (interleaved by kThr
 constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
 constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
 constexpr int kCtrlThreads = 256;
-constexpr int kSlack = 2048;  // padding elements after every workspace array
 constexpr int kGraphCacheSize = 8;
+// Check-node pass with bulk-copy staging: one block stages kTile consecutive
+// checks of one base row (kTmaVpt per thread) into shared memory.
+#ifndef QCLDPC_CN_TMA
+#define QCLDPC_CN_TMA 1
+#endif
+#ifndef QCLDPC_CN_TVPT
+#define QCLDPC_CN_TVPT 6
+#endif
+constexpr int kTmaVpt = QCLDPC_CN_TVPT;
+constexpr int kTile = kThreads * kTmaVpt;      // checks per block
+constexpr int kStage = kTile + 4;              // staged floats per row (16-byte realignment)
+constexpr int kStageWords = kTile / 32 + 4;    // staged decision words per row
+constexpr int kSmemHeader = 128;               // mbarrier, then 16-byte aligned rows
+constexpr unsigned kWaitLimit = 1u << 22;      // bounded mbarrier polls before giving up
+// Padding elements after every workspace array: lanes and staged copies that
+// run past a row's end read here (results unused), and never past the array.
+constexpr int kSlack = 4096;
 
 // Per-call arguments and workspace pointers (by value in every kernel).
 struct Work {
@@ -91,14 +110,16 @@ struct Work {
     int32_t *t;            // iteration counter of the loop
     int32_t *active;       // [F]
     int32_t *fail;         // [F] stop-test failures of the current pass
-    float *msg;            // [F][n_h][Z]
+    int32_t *err;          // device error word (a bounded wait gave up)
+    void *msg;             // [F][n_h][Z] messages in the storage format fmt
     float *L;              // [F][n_hcols][2Z]
     float *phiq;           // [F][n_d1][Z]
     uint32_t *bits;        // [2][F][n_d1][ZW]
     float *post1;          // [2][F][n_d1][Z] (soft output only)
     int64_t n, words_m, words_k;
-    int32_t n_frames, max_iter, et_start, soft, ZW;
+    int32_t n_frames, max_iter, et_start, soft, ZW, fmt;
     float clip, xmin;      // base-2 units
+    float qstep, qinv;     // int8 message quantum and its inverse (base-2 units)
 };
 static_assert(sizeof(Work) <= sizeof(((qcldpc_code *)nullptr)->last_work), "Work too large");
 
@@ -152,6 +173,30 @@ __device__ __forceinline__ float psi_f(float y) {
 constexpr uint32_t kSign = 0x80000000u;
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 
+// Storage formats of the check-to-variable messages (computation is FP32):
+// FP32, FP16 (round to nearest), or int8 codes q with m = q * qstep,
+// |q| <= 127 (values beyond saturate; the quantum is one scale for the one
+// stored edge type, heavy check-to-variable edges).
+template <typename M>
+struct Codec;
+template <>
+struct Codec<float> {
+    __device__ static float dec(float v, const Work &) { return v; }
+    __device__ static float enc(float v, const Work &) { return v; }
+};
+template <>
+struct Codec<__half> {
+    __device__ static float dec(__half v, const Work &) { return __half2float(v); }
+    __device__ static __half enc(float v, const Work &) { return __float2half_rn(v); }
+};
+template <>
+struct Codec<int8_t> {
+    __device__ static float dec(int8_t v, const Work &W) { return (float)v * W.qstep; }
+    __device__ static int8_t enc(float v, const Work &W) {
+        return (int8_t)__float2int_rn(fminf(fmaxf(v * W.qinv, -127.0f), 127.0f));
+    }
+};
+
 // ------------------------------------------------------------ kernels
 
 // Initial state: L = Q (heavy), phiq = +-Phi(|clip Q|) and the iteration-0
@@ -203,7 +248,10 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
         W.conv[f] = 0;
         W.iters[f] = 0;
     }
-    if (tid == 0) *W.t = 1;
+    if (tid == 0) {
+        *W.t = 1;
+        *W.err = 0;
+    }
 }
 
 // ---- check-node pass
@@ -252,7 +300,7 @@ __device__ __forceinline__ bool cn_row(const Table &T, const Work &W, int f, int
     uint32_t *Bc[NDa];
     {
         const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z + i0;
-        float *msg = W.msg + (size_t)f * T.n_h * Z + i0;
+        float *msg = static_cast<float *>(W.msg) + (size_t)f * T.n_h * Z + i0;
         const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z + i0;
         const uint32_t *bprev =
             W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride + (i0 >> 5);
@@ -308,7 +356,7 @@ __device__ __forceinline__ bool cn_row(const Table &T, const Work &W, int f, int
             for (int k = 0; k < NH; k++) p ^= fbits(lv[u][k]);
             bad |= valid && (p & kSign) != 0;
         }
-        if (!kUpdate) continue;
+        if constexpr (kUpdate) {
         float phi[D];
         uint32_t sg[D];
         uint32_t stot = sb[u];
@@ -355,15 +403,16 @@ __device__ __forceinline__ bool cn_row(const Table &T, const Work &W, int f, int
                 }
             }
         }
+        }
     }
     return bad;
 }
 
 // Any row shape up to MAXD circulants (heavy first), runtime degree with
 // predication; used for shapes the exact instantiations do not cover.
-template <int MAXD>
+template <int MAXD, typename M>
 __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, int f, int r, int t,
-                                               int mode) {
+                                               int mode, int i0, int vpt) {
     const bool update = mode != kTestOnly;
     const bool read_msg = mode == kSteady || mode == kSteadyTest;
     const bool test = mode == kSteadyTest || mode == kTestOnly;
@@ -371,8 +420,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
     const int rp = T.row_ptr[r];
     const int deg = T.row_ptr[r + 1] - rp;
     const int nh = T.row_nh[r];
-    const int i0 = blockIdx.x * (kThreads * kCnVpt) + threadIdx.x;
-    float *msg = W.msg + (size_t)f * T.n_h * Z;
+    M *msg = static_cast<M *>(W.msg) + (size_t)f * T.n_h * Z;
     const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
     const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
     const size_t bstride = (size_t)T.n_d1 * ZW;
@@ -380,7 +428,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
     const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
     const uint32_t *syn = W.syn + (size_t)f * W.words_m;
     bool bad = false;
-    for (int u = 0; u < kCnVpt; u++) {
+    for (int u = 0; u < vpt; u++) {
         const int i = i0 + u * kThreads;
         const bool valid = i < Z;
         const int cidx = r * Z + i;
@@ -397,7 +445,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
                 if (k < nh) {
                     const float lv = L[oa + i];
                     par ^= fbits(lv);
-                    const float d = lv - (read_msg ? msg[ob + i] : 0.0f);
+                    const float d = lv - (read_msg ? Codec<M>::dec(msg[ob + i], W) : 0.0f);
                     phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
                     sg[k] = fbits(d);
                 } else {
@@ -427,7 +475,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
             const uint32_t sk = (stot ^ sg[k]) & kSign;
             if (k < nh) {
                 const float mag = fminf(psi_f(ex), W.clip);
-                if (valid) msg[ob + i] = __uint_as_float(fbits(mag) ^ sk);
+                if (valid) msg[ob + i] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
             } else {
                 const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
                 const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
@@ -444,6 +492,276 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
         }
     }
     return bad;
+}
+
+// ---- check-node pass staged through shared memory by bulk async copies
+//
+// One block owns kTile consecutive checks (offsets i0 .. i0+kTile-1) of
+// one base row of one frame. Thread 0 arms an mbarrier and issues one
+// cp.async.bulk per operand row: the heavy posteriors at i0 + shift, the old
+// messages and the degree-1 psi values at i0, and the degree-1 decision
+// words of iteration t-1. Each source start is rounded down to 16 bytes
+// (the copy unit) and the remainder is added when reading. Every thread then
+// waits on the barrier (bounded) and evaluates its kTmaVpt checks, i0 + c *
+// kThreads + threadIdx.x, from shared memory: consecutive threads read
+// consecutive words, so the reads are free of bank conflicts.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bytes to stage for `count` elements of `esize` bytes starting at `src`
+// once the start is rounded down to 16 bytes; *rem receives the offset of
+// src[0], in elements, from that rounded start.
+__device__ __forceinline__ uint32_t stage_bytes(const void *src, uint32_t count, int esize,
+                                                int *rem) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    *rem = (int)((a & 15u) / (uintptr_t)esize);
+    return ((uint32_t)(*rem + count) * (uint32_t)esize + 15u) & ~15u;
+}
+
+// Bounded wait for the staged operands. On timeout the block records a
+// device error (decoding stops with converged = -1), waits once more
+// (bounded) for its copies, and reports failure.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, const Work &W) {
+    for (unsigned it = 0; it < kWaitLimit; it++)
+        if (mbar_try_wait(bar, 0)) return true;
+    atomicOr(W.err, 1);
+    for (unsigned it = 0; it < kWaitLimit; it++)
+        if (mbar_try_wait(bar, 0)) break;
+    return false;
+}
+
+template <int NH, int ND, int MODE, typename M>
+__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int t,
+                                        unsigned char *smem) {
+    constexpr int D = NH + ND;
+    constexpr int NHa = NH > 0 ? NH : 1;
+    constexpr int NDa = ND > 0 ? ND : 1;
+    constexpr bool kUpdate = MODE != kTestOnly;
+    constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
+    constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
+    constexpr int kWordStep = kThreads / 32;
+    const int Z = T.Z, ZW = W.ZW;
+    const int rp = T.row_ptr[r];
+    const int i0 = blockIdx.x * kTile;
+    const int tid = threadIdx.x;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *s_off = reinterpret_cast<int *>(smem + 16);  // per staged row: start of its data
+    float *stage = reinterpret_cast<float *>(smem + kSmemHeader);
+    const size_t bstride = (size_t)T.n_d1 * ZW;
+    M *msg = static_cast<M *>(W.msg) + (size_t)f * T.n_h * Z;
+
+    // Thread 0: arm the barrier, publish each staged row's read offset
+    // (row slot * kStage + 16-byte remainder), then issue the copies.
+    // Staged rows: NH posteriors, NH old messages (kReadMsg), ND psi values
+    // (kUpdate), then ND decision-word rows of kStageWords words (kTest).
+    if (tid == 0) {
+        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
+        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
+        const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const void *src[2 * NHa + 2 * NDa];
+        uint32_t nb[2 * NHa + 2 * NDa];
+        int slot_start[2 * NHa + 2 * NDa];
+        int ncopy = 0, pos = 0;
+        uint32_t total = 0;
+        // Each staged row takes row_slots 4-byte slots; s_off holds the row's
+        // first element in units of its own element size.
+        auto add = [&](const void *p, uint32_t count, int esize, int row_slots) {
+            int rem;
+            nb[ncopy] = stage_bytes(p, count, esize, &rem);
+            src[ncopy] = reinterpret_cast<const char *>(p) - esize * rem;
+            slot_start[ncopy] = pos;
+            s_off[ncopy] = pos * (4 / esize) + rem;
+            total += nb[ncopy];
+            pos += row_slots;
+            ncopy++;
+        };
+#pragma unroll
+        for (int k = 0; k < NH; k++) add(L + T.row_off_a[rp + k] + i0, kTile, 4, kStage);
+        if (kReadMsg) {
+#pragma unroll
+            for (int k = 0; k < NH; k++)
+                add(msg + T.row_off_b[rp + k] + i0, kTile, (int)sizeof(M), kStage);
+        }
+        if (kUpdate) {
+#pragma unroll
+            for (int k = 0; k < ND; k++) add(phiq + T.row_off_a[rp + NH + k] + i0, kTile, 4, kStage);
+        }
+        if (kTest) {
+#pragma unroll
+            for (int k = 0; k < ND; k++)
+                add(bprev + T.row_off_b[rp + NH + k] + (i0 >> 5), kTile / 32, 4, kStageWords);
+        }
+        mbar_expect_tx(bar, total);
+        for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
+    }
+    __syncthreads();  // barrier initialised, offsets published
+
+    // Per-row pointers for this thread's first check; check c sits at
+    // + c * kThreads elements (or + c * kWordStep words).
+    const float *pL[NHa], *pP[NDa];
+    const M *pM[NHa];
+    const uint32_t *pB[NDa];
+    {
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < NH; k++) pL[k] = stage + s_off[q++] + tid;
+        if (kReadMsg) {
+#pragma unroll
+            for (int k = 0; k < NH; k++) pM[k] = reinterpret_cast<const M *>(stage) + s_off[q++] + tid;
+        }
+        if (kUpdate) {
+#pragma unroll
+            for (int k = 0; k < ND; k++) pP[k] = stage + s_off[q++] + tid;
+        }
+        if (kTest) {
+#pragma unroll
+            for (int k = 0; k < ND; k++)
+                pB[k] = reinterpret_cast<const uint32_t *>(stage) + s_off[q++] + (tid >> 5);
+        }
+    }
+    // Output rows at this thread's first check.
+    M *oM[NHa];
+    uint32_t *oB[NDa];
+    {
+        uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
+#pragma unroll
+        for (int k = 0; k < D; k++) {
+            if (k < NH) oM[k] = msg + T.row_off_b[rp + k] + i0 + tid;
+            else oB[k - NH] = bcur + T.row_off_b[rp + k] + (i0 >> 5) + (tid >> 5);
+        }
+    }
+    const int c0 = r * Z + i0 + tid;
+    const uint32_t *sy = W.syn + (size_t)f * W.words_m + (c0 >> 5);
+    const int ssh = 31 - (c0 & 31);
+    const int dsh = 31 - (tid & 31);
+    const bool lane0 = (tid & 31) == 0;
+
+    const bool staged = stage_wait(bar, W);
+    bool bad = false;
+    if (staged) {
+#pragma unroll
+        for (int c = 0; c < kTmaVpt; c++) {
+            const int i = i0 + c * kThreads + tid;
+            const bool valid = i < Z;
+            const uint32_t sb = valid ? (__ldg(sy + c * kWordStep) << ssh) : 0u;
+            float lv[NHa], phi[D];
+            uint32_t sg[D];
+            uint32_t stot = sb, par = sb;
+#pragma unroll
+            for (int k = 0; k < NH; k++) {
+                lv[k] = pL[k][c * kThreads];
+                par ^= fbits(lv[k]);
+            }
+            if (kTest) {
+#pragma unroll
+                for (int k = 0; k < ND; k++) par ^= pB[k][c * kWordStep] << dsh;
+                bad |= valid && (par & kSign) != 0;
+            }
+            if constexpr (kUpdate) {
+#pragma unroll
+                for (int k = 0; k < NH; k++) {
+                    const float d = lv[k] - (kReadMsg ? Codec<M>::dec(pM[k][c * kThreads], W) : 0.0f);
+                    phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
+                    sg[k] = fbits(d);
+                    stot ^= sg[k];
+                }
+#pragma unroll
+                for (int k = 0; k < ND; k++) {
+                    const float p = pP[k][c * kThreads];
+                    phi[NH + k] = fabsf(p);
+                    sg[NH + k] = fbits(p);
+                    stot ^= sg[NH + k];
+                }
+                float pre[D + 1], suf[D + 1];
+                pre[0] = 0.0f;
+#pragma unroll
+                for (int k = 0; k < D; k++) pre[k + 1] = pre[k] + phi[k];
+                suf[D] = 0.0f;
+#pragma unroll
+                for (int k = D - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
+#pragma unroll
+                for (int k = 0; k < D; k++) {
+                    const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
+                    const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
+                    if (k < NH) {
+                        const float mag = fminf(psi_f(ex), W.clip);
+                        if (valid) oM[k][c * kThreads] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
+                    } else {
+                        const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
+                        const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
+                        if (lane0 && valid) oB[k - NH][c * kWordStep] = word;
+                        if (W.soft && valid) {
+                            const qc::RowEnt e = T.rows[rp + k];
+                            int vo = i + e.shift;
+                            if (vo >= Z) vo -= Z;
+                            const float mag = fminf(psi_f(ex), W.clip);
+                            float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
+                            post1[T.row_off_a[rp + k] + i] =
+                                W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
+                                kLn2 * __uint_as_float(fbits(mag) ^ sk);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) mbar_inval(bar);
+    return bad;
+}
+
+template <int MODE, typename M>
+__device__ __forceinline__ bool cn_tile_dispatch(const Table &T, const Work &W, int f, int r, int t,
+                                                 int nh, int nd, unsigned char *smem) {
+    switch (nh * 4 + nd) {
+        case 1 * 4 + 1: return cn_tile<1, 1, MODE, M>(T, W, f, r, t, smem);
+        case 2 * 4 + 0: return cn_tile<2, 0, MODE, M>(T, W, f, r, t, smem);
+        case 2 * 4 + 1: return cn_tile<2, 1, MODE, M>(T, W, f, r, t, smem);
+        case 3 * 4 + 0: return cn_tile<3, 0, MODE, M>(T, W, f, r, t, smem);
+        case 3 * 4 + 1: return cn_tile<3, 1, MODE, M>(T, W, f, r, t, smem);
+        case 4 * 4 + 0: return cn_tile<4, 0, MODE, M>(T, W, f, r, t, smem);
+        case 4 * 4 + 1: return cn_tile<4, 1, MODE, M>(T, W, f, r, t, smem);
+        default: return false;
+    }
 }
 
 template <int MODE>
@@ -490,7 +808,40 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const
             default: bad = cn_dispatch<kTestOnly>(T, W, f, r, t, nh, nd); break;
         }
     } else {
-        bad = cn_row_generic<MAXD>(T, W, f, r, t, mode);
+        bad = cn_row_generic<MAXD, float>(T, W, f, r, t, mode,
+                                          blockIdx.x * (kThreads * kCnVpt) + threadIdx.x, kCnVpt);
+    }
+    if (mode == kSteadyTest || mode == kTestOnly) {
+        if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;
+    }
+}
+
+// Check-node pass of iteration t, staged variant: grid (ceil(Z / kTile), base
+// row, frame), dynamic shared memory sized by cn_tma_smem for the code's
+// widest exact-shape row. Rows of other shapes take the register path.
+template <int MAXD, typename M>
+__global__ void __launch_bounds__(kThreads) cn_tma_kernel(const __grid_constant__ Table T,
+                                                          const __grid_constant__ Work W) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int f = blockIdx.z;
+    if (W.active[f] == 0) return;  // block-uniform
+    const int r = blockIdx.y;
+    const int t = *W.t;
+    const int mode = t > W.max_iter ? kTestOnly
+                     : t == 1       ? kFirst
+                     : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
+    const int nh = T.row_nh[r];
+    const int nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
+    bool bad;
+    if (exact_shape(nh, nd)) {
+        switch (mode) {
+            case kFirst: bad = cn_tile_dispatch<kFirst, M>(T, W, f, r, t, nh, nd, smem); break;
+            case kSteady: bad = cn_tile_dispatch<kSteady, M>(T, W, f, r, t, nh, nd, smem); break;
+            case kSteadyTest: bad = cn_tile_dispatch<kSteadyTest, M>(T, W, f, r, t, nh, nd, smem); break;
+            default: bad = cn_tile_dispatch<kTestOnly, M>(T, W, f, r, t, nh, nd, smem); break;
+        }
+    } else {
+        bad = cn_row_generic<MAXD, M>(T, W, f, r, t, mode, blockIdx.x * kTile + threadIdx.x, kTmaVpt);
     }
     if (mode == kSteadyTest || mode == kTestOnly) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;
@@ -508,9 +859,14 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
     const int t = *W.t;
     const bool last = t == W.max_iter + 1;
     const bool checked = last || (t >= 2 && t - 1 >= W.et_start);
+    const bool failed = *W.err != 0;  // a staged copy never completed: stop, flag -1
     int mine = 0;
     for (int f = threadIdx.x; f < W.n_frames; f += blockDim.x) {
-        if (W.active[f]) {
+        if (failed) {
+            W.conv[f] = -1;
+            W.iters[f] = t - 1;
+            W.active[f] = 0;
+        } else if (W.active[f]) {
             if (checked && W.fail[f] == 0) {
                 W.conv[f] = 1;
                 W.iters[f] = t - 1;
@@ -537,6 +893,7 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 // Grid (tile, heavy column, frame). Lanes past the end of the column read
 // message padding (never stored); the channel LLRs, the caller's buffer, are
 // read only in range.
+template <typename M>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
                                                       const __grid_constant__ Work W) {
     const int f = blockIdx.z;
@@ -544,7 +901,7 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     const int Z = T.Z;
     const int hc = blockIdx.y;
     const int j0 = blockIdx.x * (kThreads * kVnVpt) + threadIdx.x;
-    const float *__restrict__ msg = W.msg + (size_t)f * T.n_h * Z;
+    const M *__restrict__ msg = static_cast<const M *>(W.msg) + (size_t)f * T.n_h * Z;
     const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
     float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
     float acc[kVnVpt];
@@ -557,12 +914,12 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
 #pragma unroll kVnUnroll
     for (int k = T.col_ptr[hc]; k < ce; k++) {
         const qc::ColEnt e = T.cols[k];
-        const float *__restrict__ mk = msg + e.id * Z;
+        const M *__restrict__ mk = msg + e.id * Z;
 #pragma unroll
         for (int u = 0; u < kVnVpt; u++) {
             int idx = j0 + u * kThreads - e.shift;
             if (idx < 0) idx += Z;
-            acc[u] += mk[idx];
+            acc[u] += Codec<M>::dec(mk[idx], W);
         }
     }
 #pragma unroll
@@ -641,12 +998,14 @@ __global__ void replay_prep_kernel(const __grid_constant__ Work W) {
 // ------------------------------------------------------------ host side
 
 struct Layout {
-    size_t t, active, fail, msg, L, phiq, bits, post1, total;
+    size_t t, err, active, fail, msg, L, phiq, bits, post1, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-Layout layout_of(const Table &T, int F, bool soft) {
+size_t msg_elem_size(int fmt) { return fmt == 2 ? 1 : fmt == 1 ? 2 : 4; }
+
+Layout layout_of(const Table &T, int F, bool soft, int fmt) {
     Layout o;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -656,9 +1015,10 @@ Layout layout_of(const Table &T, int F, bool soft) {
     };
     const size_t Z = (size_t)T.Z, ZW = (Z + 31) / 32;
     o.t = take(sizeof(int32_t));
+    o.err = take(sizeof(int32_t));
     o.active = take(sizeof(int32_t) * F);
     o.fail = take(sizeof(int32_t) * F);
-    o.msg = take(sizeof(float) * (F * T.n_h * Z + kSlack));
+    o.msg = take(msg_elem_size(fmt) * (F * T.n_h * Z + kSlack));
     o.L = take(sizeof(float) * (F * T.n_hcols * 2 * Z + kSlack));
     o.phiq = take(sizeof(float) * (F * T.n_d1 * Z + kSlack));
     o.bits = take(sizeof(uint32_t) * (2 * F * T.n_d1 * ZW + kSlack));
@@ -690,6 +1050,69 @@ void *cn_kernel_for(int maxdeg) {
     return (void *)cn_kernel<16>;
 }
 
+template <typename M>
+void *cn_tma_kernel_for_fmt(int maxdeg) {
+    if (maxdeg <= 5) return (void *)cn_tma_kernel<5, M>;
+    if (maxdeg <= 8) return (void *)cn_tma_kernel<8, M>;
+    return (void *)cn_tma_kernel<16, M>;
+}
+
+void *cn_tma_kernel_for(int maxdeg, int fmt) {
+    if (fmt == 1) return cn_tma_kernel_for_fmt<__half>(maxdeg);
+    if (fmt == 2) return cn_tma_kernel_for_fmt<int8_t>(maxdeg);
+    return cn_tma_kernel_for_fmt<float>(maxdeg);
+}
+
+void *vn_kernel_for(int fmt) {
+    if (fmt == 1) return (void *)vn_kernel<__half>;
+    if (fmt == 2) return (void *)vn_kernel<int8_t>;
+    return (void *)vn_kernel<float>;
+}
+
+template <typename M>
+void raise_smem_cap(int cap) {
+    cudaFuncSetAttribute((const void *)cn_tma_kernel<5, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute((const void *)cn_tma_kernel<8, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+    cudaFuncSetAttribute((const void *)cn_tma_kernel<16, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+}
+
+// Launch of the check-node pass for a code: kernel, grid and dynamic shared
+// memory (the staged variant needs the code's widest exact-shape row).
+struct CnLaunch {
+    void *func;
+    dim3 grid;
+    size_t smem;
+};
+
+CnLaunch cn_launch(const Table &T, int F, int fmt) {
+    CnLaunch c;
+    if (QCLDPC_CN_TMA || fmt != 0) {
+        size_t smem = kSmemHeader;
+        for (int r = 0; r < T.mb; r++) {
+            const int nh = T.row_nh[r], nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
+            if (!exact_shape(nh, nd)) continue;
+            const size_t b = kSmemHeader + (size_t)(2 * nh + nd) * kStage * 4 + (size_t)nd * kStageWords * 4;
+            smem = std::max(smem, b);
+        }
+        c.func = cn_tma_kernel_for(T.max_row_deg, fmt);
+        c.grid = dim3((unsigned)((T.Z + kTile - 1) / kTile), (unsigned)T.mb, (unsigned)F);
+        c.smem = smem;
+        // Capacity for the largest staged row set (4 heavy + 1 degree-1).
+        static std::once_flag once;
+        std::call_once(once, [] {
+            const int cap = kSmemHeader + 9 * kStage * 4 + kStageWords * 4;
+            raise_smem_cap<float>(cap);
+            raise_smem_cap<__half>(cap);
+            raise_smem_cap<int8_t>(cap);
+        });
+    } else {
+        c.func = cn_kernel_for(T.max_row_deg);
+        c.grid = cn_grid(T, F);
+        c.smem = 0;
+    }
+    return c;
+}
+
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -710,12 +1133,13 @@ void free_entry(GraphEntry &g) {
 }
 
 cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep,
-                       size_t ndep, void *func, dim3 grid, dim3 block, void **args) {
+                       size_t ndep, void *func, dim3 grid, dim3 block, void **args,
+                       size_t smem = 0) {
     cudaKernelNodeParams kp = {};
     kp.func = func;
     kp.gridDim = grid;
     kp.blockDim = block;
-    kp.sharedMemBytes = 0;
+    kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
     kp.extra = nullptr;
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
@@ -750,15 +1174,16 @@ int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
         return qc::cuda_fail(err, "decode: add conditional node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     cudaGraphNode_t n_cn, n_ctrl, n_vn;
-    if ((err = add_kernel(&n_cn, body, nullptr, 0, cn_kernel_for(T.max_row_deg), cn_grid(T, F),
-                          dim3(kThreads), args)) != cudaSuccess)
+    const CnLaunch cl = cn_launch(T, F, w0.fmt);
+    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, dim3(kThreads), args,
+                          cl.smem)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add check-node kernel");
     void *ctrl_args[] = {&wcopy, &handle};
     if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                           dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add control kernel");
-    if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, (void *)vn_kernel, vn_grid(T, F), dim3(kThreads),
-                          args)) != cudaSuccess)
+    if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
+                          dim3(kThreads), args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add variable-node kernel");
     if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks),
                           dim3(kThreads), args)) != cudaSuccess)
@@ -777,18 +1202,18 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
     const int F = w.n_frames;
     const int blocks = sm_count() * 4;
     init_kernel<<<blocks, kThreads, 0, stream>>>(T, w);
-    void *cn = cn_kernel_for(T.max_row_deg);
+    const CnLaunch cl = cn_launch(T, F, w.fmt);
     Table tcopy = T;
     Work wcopy = w;
     void *args[] = {&tcopy, &wcopy};
     cudaGraphConditionalHandle none = 0;
     cudaError_t err = cudaGetLastError();
     for (int t = 1; t <= w.max_iter + 1 && err == cudaSuccess; t++) {
-        err = cudaLaunchKernel(cn, cn_grid(T, F), dim3(kThreads), args, 0, stream);
+        err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
         if (t <= w.max_iter)
-            err = cudaLaunchKernel((void *)vn_kernel, vn_grid(T, F), dim3(kThreads), args, 0, stream);
+            err = cudaLaunchKernel(vn_kernel_for(w.fmt), vn_grid(T, F), dim3(kThreads), args, 0, stream);
         if (err == cudaSuccess) err = cudaGetLastError();
     }
     if (err == cudaSuccess) {
@@ -812,9 +1237,10 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     const bool soft = post != nullptr;
     if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode: n_frames must be in [0, 65535]");
     if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
-    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format != 0 || p.reserved ||
-        (p.launch_mode != 0 && p.launch_mode != 1))
-        return fail(QCLDPC_E_INVAL, "decode: unsupported option (phi_floor > 0, flooding, FP32)");
+    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format < 0 || p.msg_format > 2 ||
+        !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1))
+        return fail(QCLDPC_E_INVAL,
+                    "decode: unsupported option (phi_floor > 0, flooding, msg_format 0..2, msg_step >= 0)");
     if (soft && p.soft_output != 1)
         return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
     if (F == 0) return QCLDPC_OK;
@@ -830,7 +1256,7 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode: current device differs from the code's device");
 
     const Table &T = code->tab;
-    const Layout lo = layout_of(T, F, soft);
+    const Layout lo = layout_of(T, F, soft, p.msg_format);
     if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
     char *base = static_cast<char *>(ws);
     Work w;
@@ -844,7 +1270,8 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.t = reinterpret_cast<int32_t *>(base + lo.t);
     w.active = reinterpret_cast<int32_t *>(base + lo.active);
     w.fail = reinterpret_cast<int32_t *>(base + lo.fail);
-    w.msg = reinterpret_cast<float *>(base + lo.msg);
+    w.err = reinterpret_cast<int32_t *>(base + lo.err);
+    w.msg = base + lo.msg;
     w.L = reinterpret_cast<float *>(base + lo.L);
     w.phiq = reinterpret_cast<float *>(base + lo.phiq);
     w.bits = reinterpret_cast<uint32_t *>(base + lo.bits);
@@ -859,6 +1286,13 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.ZW = (T.Z + 31) / 32;
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;  // base-2 units
     w.xmin = p.phi_floor * kLog2e;
+    w.fmt = p.msg_format;
+    if (w.fmt == 2) {
+        // int8 quantum: msg_step natural-LLR units, default clip / 127
+        const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;
+        w.qstep = step * kLog2e;
+        w.qinv = 1.0f / w.qstep;
+    }
 
     std::lock_guard<std::mutex> lock(code->mu);
     code->last_ws = ws;
@@ -910,7 +1344,9 @@ extern "C" size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
                                           const qcldpc_params *p) {
     if (!code || n_frames < 0) return 0;
     const bool soft = p && p->soft_output == 1;
-    return layout_of(code->tab, n_frames, soft).total;
+    const int fmt = p ? p->msg_format : 0;
+    if (fmt < 0 || fmt > 2) return 0;
+    return layout_of(code->tab, n_frames, soft, fmt).total;
 }
 
 extern "C" int qcldpc_decode(const qcldpc_code *code, const float *llr_dev,
@@ -947,10 +1383,10 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     std::lock_guard<std::mutex> lock(code->mu);
     if (code->last_ws != workspace_dev || code->last_frames != n_frames)
         return fail(QCLDPC_E_INVAL, "time_passes: no decode ran on this workspace with this frame count");
-    const Layout lo = layout_of(code->tab, n_frames, code->last_soft != 0);
-    if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "time_passes: workspace too small");
     Work w;
     std::memcpy(&w, code->last_work, sizeof(w));
+    const Layout lo = layout_of(code->tab, n_frames, code->last_soft != 0, w.fmt);
+    if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "time_passes: workspace too small");
     if (w.max_iter < 2) w.max_iter = 2;  // replays run as iteration 2: a full update
     cudaEvent_t ev[3];
     cudaError_t err = cudaSuccess;
@@ -958,15 +1394,16 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
         if ((err = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(err, "time_passes: cudaEventCreate");
     const Table &T = code->tab;
     replay_prep_kernel<<<1, 256, 0, stream>>>(w);
-    void *cn = cn_kernel_for(T.max_row_deg);
+    const CnLaunch cl = cn_launch(T, n_frames, w.fmt);
     Table tcopy = T;
     void *args[] = {&tcopy, &w};
     cudaEventRecord(ev[0], stream);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel(cn, cn_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+        err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
     cudaEventRecord(ev[1], stream);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel((void *)vn_kernel, vn_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+        err = cudaLaunchKernel(vn_kernel_for(w.fmt), vn_grid(T, n_frames), dim3(kThreads), args, 0,
+                               stream);
     cudaEventRecord(ev[2], stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -1008,7 +1445,7 @@ extern "C" int qcldpc_decode_noalloc(const qcldpc_code *code, const float *llr_d
     using namespace qc;
     if (!code) return fail(QCLDPC_E_INVAL, "decode_noalloc: code is NULL");
     if (n_frames < 0) return fail(QCLDPC_E_INVAL, "decode_noalloc: negative frame count");
-    const size_t need = layout_of(code->tab, n_frames, false).total;
+    const size_t need = layout_of(code->tab, n_frames, false, p ? p->msg_format : 0).total;
     if (need > kNoallocScratchBytes)
         return fail(QCLDPC_E_UNSUPPORTED,
                     "decode_noalloc: this code and frame count need " + std::to_string(need) +

@@ -47,7 +47,7 @@ class qcldpc_params(ctypes.Structure):
         ("msg_format", ctypes.c_int32),
         ("soft_output", ctypes.c_int32),
         ("launch_mode", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("msg_step", ctypes.c_float),
     ]
 
 

@@ -1,0 +1,114 @@
+"""Low-precision message storage (FP16, scaled int8) against the FP64 oracle.
+
+All arithmetic stays FP32; only the stored check-to-variable messages change.
+The error bars asserted here are measured properties of each format, stated
+next to the FP32 bar of test_gpu_parity (1e-3 relative):
+* FP16: every message is rounded to 11 significant bits; the rounding
+  compounds through the iterations, and posteriors after 50 iterations at
+  SNR 0.029 stay within 5e-2 relative (scaled as in test_gpu_parity;
+  measured 2.1-2.3e-2 max, 1.7-2.1e-2 at p99.9 on two frames);
+* int8 with quantum d: after one iteration each of a node's messages is off
+  by at most d/2, so |L_gpu - L_ref| <= deg(v) d / 2 (+ FP32 slack).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from frames import make_frames
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1702_07740_gb300 import qcldpc as q  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device visible")
+    q.load()
+
+
+def _llr(fr):
+    n = fr.x32.size
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    q.qcldpc_llr_8d(torch.from_numpy(fr.x32.reshape(-1)).cuda(),
+                    torch.from_numpy(fr.m32.reshape(-1)).cuda(), n, fr.snr, out)
+    return out
+
+
+def _decode(code, fr, llr, iters, fmt, step=0.0, et_start=None):
+    params = q.qcldpc_params_init(soft_output=1, msg_format=fmt, msg_step=step)
+    if et_start is not None:
+        params.et_start = et_start
+    dec = q.Decoder(code, fr.F, params, soft=True)
+    syn = torch.from_numpy(synth.pack_bits(fr.syn).view(np.int32).reshape(-1)).cuda()
+    dec.decode(llr, syn, iters)
+    torch.cuda.synchronize()
+    wk = (code.k + 31) // 32
+    keys = synth.unpack_bits(dec.keys.cpu().numpy().view(np.uint32).reshape(fr.F, wk), code.k)
+    return (keys, dec.converged.cpu().numpy(), dec.iters.cpu().numpy(),
+            dec.posterior.cpu().numpy().reshape(fr.F, code.n).astype(np.float64))
+
+
+def test_fp16_posteriors_after_50_iterations():
+    fr = make_frames(synth.rate002_code(512), 0.029, 2)
+    code = q.create_code_from(fr.code_dict)
+    llr = _llr(fr)
+    _, _, _, post = _decode(code, fr, llr, 50, fmt=1, et_start=51)
+    for f in range(fr.F):
+        ref, _, _, _ = oracle.decode(fr.code, fr.q64[f], fr.syn[f], 50, et_start=51)
+        err = np.abs(post[f] - ref) / np.maximum(np.abs(ref), 0.1)
+        print(f"FP16 frame {f}: max scaled err {err.max():.2e}, p99.9 {np.quantile(err, 0.999):.2e}")
+        assert err.max() <= 5e-2
+
+
+@pytest.mark.parametrize("step", [0.05, 0.118])
+def test_int8_one_iteration_error_is_within_half_a_quantum_per_message(step):
+    fr = make_frames(synth.rate002_code(512), 0.029, 1)
+    code = q.create_code_from(fr.code_dict)
+    _, _, _, post = _decode(code, fr, _llr(fr), 1, fmt=2, step=step, et_start=2)
+    ref, _, _, _ = oracle.decode(fr.code, fr.q64[0], fr.syn[0], 1, et_start=2)
+    deg = np.bincount(fr.code.edge_vn, minlength=fr.code.n)
+    bound = deg * step / 2 + 1e-4 * np.maximum(np.abs(ref), 1.0)
+    err = np.abs(post[0] - ref)
+    print(f"int8 step {step}: max |err| {err.max():.3e}, max err/bound {(err / bound).max():.2f}")
+    assert np.all(err <= bound)
+
+
+def test_fp16_decisions_match_fp32_on_converging_frames():
+    """At an SNR where frames converge, FP16 storage changes neither the stop
+    iteration nor the key bits of these frames."""
+    fr = make_frames(synth.rate002_code(2000), 0.15, 4)
+    code = q.create_code_from(fr.code_dict)
+    llr = _llr(fr)
+    k32, c32, i32, _ = _decode(code, fr, llr, 60, fmt=0)
+    k16, c16, i16, _ = _decode(code, fr, llr, 60, fmt=1)
+    assert c32.sum() >= 1
+    np.testing.assert_array_equal(c16, c32)
+    for f in range(fr.F):
+        if c32[f]:
+            np.testing.assert_array_equal(k16[f], k32[f])
+
+
+def test_int8_decodes_converging_frames():
+    fr = make_frames(synth.rate002_code(2000), 0.2, 4)
+    code = q.create_code_from(fr.code_dict)
+    k8, c8, i8, _ = _decode(code, fr, _llr(fr), 100, fmt=2)
+    assert c8.sum() >= 3
+    for f in range(fr.F):
+        if c8[f]:
+            chat_ok = (k8[f] == fr.bits[f][: fr.code.k]).mean()
+            assert chat_ok > 0.99
+
+
+def test_bad_message_format_is_rejected():
+    code = q.create_code_from(synth.rate002_code(64))
+    assert q.qcldpc_decode_workspace(code, 1, q.qcldpc_params_init(msg_format=3)) == 0
+    dec = q.Decoder(code, 1)
+    x = torch.zeros(code.n, device="cuda")
+    s = torch.zeros((code.m + 31) // 32, dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QcldpcError, match="INVAL"):
+        q.qcldpc_decode(code, x, s, 1, 5, q.qcldpc_params_init(msg_format=5), dec.keys,
+                        dec.converged, dec.iters, dec.workspace, dec.ws_bytes)
