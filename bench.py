@@ -69,6 +69,23 @@ def dist_env():
     return world, rank, local
 
 
+def replica_seed(rank: int, batch: int, frame: int, batches: int, frames: int) -> int:
+    """Seed of one frame of one rank: ranks decode disjoint seeded frames
+    (replicas, weak scaling; no data is exchanged between ranks)."""
+    return synth.frame_seed((rank * batches + batch) * frames + frame)
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Largest value over all ranks (the timing rule: the slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def wilson(k, n, z=1.96):
     if n == 0:
         return (float("nan"), float("nan"))
@@ -271,7 +288,7 @@ def run_ours(args, world, rank, local):
     for b in range(B):
         xs, ys, bs = [], [], []
         for f in range(F):
-            seed = synth.frame_seed((rank * B + b) * F + f)
+            seed = replica_seed(rank, b, f, B, F)
             x, y, bits = synth.channel_frame(n, args.snr, seed)
             xs.append(x.astype(np.float32)); ys.append(y.astype(np.float32)); bs.append(bits)
         x_h = torch.from_numpy(np.concatenate(xs)).pin_memory()
@@ -327,9 +344,7 @@ def run_ours(args, world, rank, local):
     elapsed = evs[0].elapsed_time(evs[-1]) / 1e3
     if world > 1:
         dist.barrier()
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+        elapsed = max_over_ranks(elapsed, dev)
     clocks = sampler.stop() if sampler else None
     value = world * args.steps * F * n / elapsed / 1e6
 
@@ -382,9 +397,7 @@ def run_ours(args, world, rank, local):
     e1.synchronize()
     e2e_elapsed = e0.elapsed_time(e1) / 1e3
     if world > 1:
-        t = torch.tensor([e2e_elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_elapsed = float(t.item())
+        e2e_elapsed = max_over_ranks(e2e_elapsed, dev)
     e2e_value = world * args.steps * F * n / e2e_elapsed / 1e6
     h2d = 2 * F * n * 4 + F * wm * 4
     d2h = F * wk * 4 + 2 * F * 4

@@ -123,6 +123,22 @@ int qcldpc_bob_message_8d(const float *y_dev, const uint32_t *bits_dev,
 int qcldpc_llr_8d(const float *x_dev, const float *m_dev, int64_t n, float snr,
                   float *llr_dev, qcldpc_stream_t stream);
 
+/*
+ * The d-dimensional maps for d in {1, 2, 4, 8} (Sec. II-C, multi-dimensional
+ * reconciliation): groups of d consecutive positions share one virtual
+ * BIAWGN channel. Bob: M = U Y with U_j = (-1)^{C_j} (reals, complex
+ * numbers, quaternions, octonions by Cayley-Dickson doubling). Alice:
+ * R = M conj(X) / |X|^2, sigma_N^2 = d sigma_Z^2 / |X|^2, Q = 2R / sigma_N^2
+ * = (M conj(X)) 2 snr / d; for d = 1 this is Step 1 of Algorithm 1 with
+ * sigma_N^2 = sigma_Z^2 / X^2. d = 8 calls the 8-D entry points above.
+ * Arrays as for the 8-D calls (n % d == 0); 4-byte alignment suffices for
+ * d < 8. Errors: QCLDPC_E_INVAL, _ALIGN, _CUDA.
+ */
+int qcldpc_bob_message(int d, const float *y_dev, const uint32_t *bits_dev, int64_t n,
+                       float *m_dev, qcldpc_stream_t stream);
+int qcldpc_llr(int d, const float *x_dev, const float *m_dev, int64_t n, float snr,
+               float *llr_dev, qcldpc_stream_t stream);
+
 /* Decoder options. Initialise with qcldpc_params_init. */
 typedef struct qcldpc_params {
     float clip;          /* every edge message is clipped to [-clip, clip];
@@ -202,6 +218,51 @@ int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
                        int32_t *converged_dev, int32_t *iters_dev,
                        float *posterior_dev, void *workspace_dev,
                        size_t workspace_bytes, qcldpc_stream_t stream);
+
+/*
+ * Pools: continuous batching of frames of one code (serving). A pool is a
+ * fixed set of n_slots frame slots with all decoder state in one caller-owned
+ * workspace (qcldpc_pool_workspace bytes, 256-byte aligned). Frames are loaded
+ * into free slots at any time; each step runs n_passes iteration passes over
+ * all running slots, every frame at its own iteration and with its own stop
+ * test (the rule of qcldpc_decode, max_iter and options fixed per pool);
+ * frames that stopped are collected, which frees their slots. A frame's
+ * result does not depend on the other frames sharing the passes.
+ *
+ *   qcldpc_pool_create   max_iter >= 0; p as for qcldpc_decode (soft_output
+ *                        must be 0); all slots start free. Enqueues a reset on
+ *                        `stream`. Host handle, library-owned.
+ *   qcldpc_pool_state    device pointer to int32[n_slots] slot states:
+ *                        0 free, 1 running, 2 stopped (result ready)
+ *   qcldpc_pool_load     n frames: slots_dev int32[n] (free or stopped slots,
+ *                        distinct), llr_dev float[n * code n] (natural LLRs),
+ *                        syn_dev uint32[n * ceil(m/32)]; inputs are copied, so
+ *                        the caller may reuse them once the load has run
+ *   qcldpc_pool_step     n_passes >= 1 passes; the graph is cached per count
+ *   qcldpc_pools_step    one graph stepping several pools concurrently (e.g.
+ *                        codes of different rates), cached per pool list
+ *   qcldpc_pool_collect  for n stopped slots: key bits uint32[n * ceil(k/32)],
+ *                        converged int32[n] (1, 0, or -1 if a device wait
+ *                        timed out), iterations int32[n]; frees the slots
+ * All calls only enqueue work on `stream`. Calls on one pool are serialised
+ * on the host; GPU work of one pool must stay on one stream (or be ordered by
+ * the caller). Errors: QCLDPC_E_INVAL, _ALIGN, _NOMEM, _CUDA.
+ */
+typedef struct qcldpc_pool qcldpc_pool;
+size_t qcldpc_pool_workspace(const qcldpc_code *code, int n_slots, const qcldpc_params *p);
+int qcldpc_pool_create(const qcldpc_code *code, int n_slots, int max_iter, const qcldpc_params *p,
+                       void *workspace_dev, size_t workspace_bytes, qcldpc_stream_t stream,
+                       qcldpc_pool **out);
+void qcldpc_pool_destroy(qcldpc_pool *pool);
+int qcldpc_pool_state(const qcldpc_pool *pool, const int32_t **state_dev);
+int qcldpc_pool_load(qcldpc_pool *pool, int n, const int32_t *slots_dev, const float *llr_dev,
+                     const uint32_t *syn_dev, qcldpc_stream_t stream);
+int qcldpc_pool_step(qcldpc_pool *pool, int n_passes, qcldpc_stream_t stream);
+int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_passes,
+                      qcldpc_stream_t stream);
+int qcldpc_pool_collect(qcldpc_pool *pool, int n, const int32_t *slots_dev,
+                        uint32_t *key_bits_dev, int32_t *converged_dev, int32_t *iters_dev,
+                        qcldpc_stream_t stream);
 
 /*
  * Measurement helper; the paper has no counterpart. Replays the check-node

@@ -52,6 +52,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include <cuda_fp16.h>
 
@@ -107,7 +108,8 @@ struct Work {
     int32_t *conv;         // [F]
     int32_t *iters;        // [F]
     float *post;           // [F][n] or nullptr
-    int32_t *t;            // iteration counter of the loop
+    int32_t *t;            // [F] iteration each frame is at
+    int32_t *state;        // [F] slot state for pools (0 free, 1 running, 2 stopped) or null
     int32_t *active;       // [F]
     int32_t *fail;         // [F] stop-test failures of the current pass
     int32_t *err;          // device error word (a bounded wait gave up)
@@ -247,11 +249,9 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
         W.fail[f] = 0;
         W.conv[f] = 0;
         W.iters[f] = 0;
+        W.t[f] = 1;
     }
-    if (tid == 0) {
-        *W.t = 1;
-        *W.err = 0;
-    }
+    if (tid == 0) *W.err = 0;
 }
 
 // ---- check-node pass
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
     const int r = blockIdx.y;
-    const int t = *W.t;
+    const int t = W.t[f];
     const int mode = t > W.max_iter ? kTestOnly
                      : t == 1       ? kFirst
                      : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
@@ -826,7 +826,7 @@ __global__ void __launch_bounds__(kThreads) cn_tma_kernel(const __grid_constant_
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
     const int r = blockIdx.y;
-    const int t = *W.t;
+    const int t = W.t[f];
     const int mode = t > W.max_iter ? kTestOnly
                      : t == 1       ? kFirst
                      : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
@@ -848,45 +848,48 @@ __global__ void __launch_bounds__(kThreads) cn_tma_kernel(const __grid_constant_
     }
 }
 
-// Loop control, one block: apply the stop test of iteration t-1, count t up,
-// and keep the WHILE node running while any frame is active.
+// Loop control, one block: apply each frame's stop test of its iteration
+// t-1, count running frames on, and (inside the decode graph) keep the WHILE
+// node running while any frame is active. Frames carry their own iteration
+// counter, so frames loaded at different times (pools) share the passes.
 template <bool kInGraph>
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constant__ Work W,
                                                             cudaGraphConditionalHandle handle) {
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
-    const int t = *W.t;
-    const bool last = t == W.max_iter + 1;
-    const bool checked = last || (t >= 2 && t - 1 >= W.et_start);
     const bool failed = *W.err != 0;  // a staged copy never completed: stop, flag -1
     int mine = 0;
     for (int f = threadIdx.x; f < W.n_frames; f += blockDim.x) {
-        if (failed) {
-            W.conv[f] = -1;
-            W.iters[f] = t - 1;
-            W.active[f] = 0;
-        } else if (W.active[f]) {
-            if (checked && W.fail[f] == 0) {
+        if (W.active[f]) {
+            const int t = W.t[f];
+            const bool last = t == W.max_iter + 1;
+            const bool checked = last || (t >= 2 && t - 1 >= W.et_start);
+            bool stop = true;
+            if (failed) {
+                W.conv[f] = -1;
+                W.iters[f] = t - 1;
+            } else if (checked && W.fail[f] == 0) {
                 W.conv[f] = 1;
                 W.iters[f] = t - 1;
-                W.active[f] = 0;
             } else if (last) {
                 W.conv[f] = 0;
                 W.iters[f] = W.max_iter;
-                W.active[f] = 0;
             } else {
+                stop = false;
+                W.t[f] = t + 1;
                 mine = 1;
+            }
+            if (stop) {
+                W.active[f] = 0;
+                if (W.state) W.state[f] = 2;
             }
         }
         W.fail[f] = 0;
     }
     if (mine) atomicOr(&any, 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        *W.t = t + 1;
-        if (kInGraph) cudaGraphSetConditional(handle, any ? 1u : 0u);
-    }
+    if (kInGraph && threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
 }
 
 // Variable-node pass: L_v = Q_v + sum_c m_cv for every heavy variable node.
@@ -991,8 +994,10 @@ __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__
 // every frame active) so that a replayed check-node pass does a full update.
 __global__ void replay_prep_kernel(const __grid_constant__ Work W) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid == 0) *W.t = 2;
-    for (int f = tid; f < W.n_frames; f += gridDim.x * blockDim.x) W.active[f] = 1;
+    for (int f = tid; f < W.n_frames; f += gridDim.x * blockDim.x) {
+        W.active[f] = 1;
+        W.t[f] = 2;
+    }
 }
 
 // ------------------------------------------------------------ host side
@@ -1014,7 +1019,7 @@ Layout layout_of(const Table &T, int F, bool soft, int fmt) {
         return at;
     };
     const size_t Z = (size_t)T.Z, ZW = (Z + 31) / 32;
-    o.t = take(sizeof(int32_t));
+    o.t = take(sizeof(int32_t) * F);
     o.err = take(sizeof(int32_t));
     o.active = take(sizeof(int32_t) * F);
     o.fail = take(sizeof(int32_t) * F);
@@ -1414,6 +1419,445 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     *cn_ms = a / reps;
     *vn_ms = b / reps;
     clear_error();
+    return QCLDPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pools: continuous batching of frames of one code.
+//
+// A pool is a fixed set of frame slots of one code, with the decoder state of
+// every slot in one caller-owned workspace. Frames are loaded into free slots
+// at any time, every step runs a given number of iteration passes over all
+// running slots (each frame at its own iteration), and frames that stopped are
+// collected, which frees their slots. Because every slot keeps its own
+// counter, stop test and outputs, a frame decodes exactly as it would alone,
+// whatever else shares the passes.
+namespace {
+
+__global__ void __launch_bounds__(kThreads) pool_reset_kernel(const __grid_constant__ Work W) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t f = tid; f < W.n_frames; f += (int64_t)gridDim.x * blockDim.x) {
+        W.state[f] = 0;
+        W.active[f] = 0;
+        W.fail[f] = 0;
+        W.t[f] = 0;
+        W.conv[f] = 0;
+        W.iters[f] = 0;
+    }
+    if (tid == 0) *W.err = 0;
+}
+
+// Copy n frames (channel LLRs, syndromes) into the listed slots and set up
+// their decoder state as init_kernel does for a whole batch.
+__global__ void __launch_bounds__(kThreads) pool_load_kernel(const __grid_constant__ Table T,
+                                                             const __grid_constant__ Work W,
+                                                             const int32_t *__restrict__ slots, int n,
+                                                             const float *__restrict__ llr_src,
+                                                             const uint32_t *__restrict__ syn_src) {
+    const int Z = T.Z;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t N = W.n;
+    for (int64_t e = tid; e < (int64_t)n * N; e += nthreads) {
+        const int64_t q = e / N, v = e - q * N;
+        const_cast<float *>(W.llr)[(int64_t)slots[q] * N + v] = llr_src[e];
+    }
+    for (int64_t e = tid; e < (int64_t)n * W.words_m; e += nthreads) {
+        const int64_t q = e / W.words_m, w = e - q * W.words_m;
+        const_cast<uint32_t *>(W.syn)[(int64_t)slots[q] * W.words_m + w] = syn_src[e];
+    }
+    const int64_t nL = (int64_t)n * T.n_hcols * Z;
+    for (int64_t e = tid; e < nL; e += nthreads) {
+        const int64_t q = e / ((int64_t)T.n_hcols * Z);
+        const int64_t rem = e - q * T.n_hcols * Z;
+        const int hc = (int)(rem / Z), j = (int)(rem - (int64_t)hc * Z);
+        const int64_t f = slots[q];
+        const float qv = llr_src[q * N + (int64_t)T.hcol_base[hc] * Z + j] * kLog2e + 0.0f;
+        float *row = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+        row[j] = qv;
+        row[j + Z] = qv;
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    const int64_t nwords = (int64_t)n * T.n_d1 * W.ZW;
+    for (int64_t qw = warp; qw < nwords; qw += nwarps) {
+        const int64_t q = qw / ((int64_t)T.n_d1 * W.ZW);
+        const int64_t rem = qw - q * T.n_d1 * W.ZW;
+        const int k = (int)(rem / W.ZW), wd = (int)(rem - (int64_t)k * W.ZW);
+        const int64_t f = slots[q];
+        const int i = wd * 32 + lane;
+        bool neg = false;
+        if (i < Z) {
+            int vo = i + T.d1_shift[k];
+            if (vo >= Z) vo -= Z;
+            const float qv = llr_src[q * N + (int64_t)T.d1_col[k] * Z + vo];
+            const float a = fmaxf(fminf(fabsf(qv) * kLog2e, W.clip), W.xmin);
+            const float p = psi_f(a);
+            W.phiq[((size_t)f * T.n_d1 + k) * Z + i] = qv < 0.0f ? -p : p;
+            neg = qv < 0.0f;
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, neg);
+        if (lane == 0) {
+            // decisions of iteration 0 go to the buffer of parity 0
+            W.bits[((size_t)f * T.n_d1 + k) * W.ZW + wd] = word;
+        }
+    }
+    for (int64_t q = tid; q < n; q += nthreads) {
+        const int32_t f = slots[q];
+        W.t[f] = 1;
+        W.fail[f] = 0;
+        W.conv[f] = 0;
+        W.iters[f] = 0;
+        W.active[f] = 1;
+        W.state[f] = 1;
+    }
+}
+
+// Outputs of the listed (stopped) slots, then free them.
+__global__ void __launch_bounds__(kThreads) pool_collect_kernel(
+    const __grid_constant__ Table T, const __grid_constant__ Work W, const int32_t *__restrict__ slots,
+    int n, uint32_t *__restrict__ keys, int32_t *__restrict__ conv, int32_t *__restrict__ iters) {
+    const int Z = T.Z;
+    const int lane = threadIdx.x & 31;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
+    for (int64_t qw = warp; qw < (int64_t)n * W.words_k; qw += nwarps) {
+        const int64_t q = qw / W.words_k, wd = qw - q * W.words_k;
+        const int64_t f = slots[q];
+        const int64_t v = wd * 32 + lane;
+        bool dec = false;
+        if (v < T.k) {
+            const int c = (int)(v / Z), j = (int)(v - (int64_t)c * Z);
+            const int kind = T.col_kind[c];
+            if (kind >= 0) {
+                dec = W.L[((size_t)f * T.n_hcols + kind) * 2 * Z + j] < 0.0f;
+            } else {
+                const int d = -kind - 2;
+                int i = j - T.d1_shift[d];
+                if (i < 0) i += Z;
+                const int b = W.iters[f] & 1;
+                const uint32_t word =
+                    W.bits[(((size_t)b * W.n_frames + f) * T.n_d1 + d) * W.ZW + (i >> 5)];
+                dec = (word >> (i & 31)) & 1u;
+            }
+        }
+        const uint32_t word = __ballot_sync(0xffffffffu, dec);
+        if (lane == 0) keys[q * W.words_k + wd] = word;
+    }
+    for (int64_t q = tid; q < n; q += nthreads) {
+        const int32_t f = slots[q];
+        conv[q] = W.conv[f];
+        iters[q] = W.iters[f];
+    }
+}
+
+__global__ void pool_free_kernel(const __grid_constant__ Work W, const int32_t *__restrict__ slots,
+                                 int n) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t q = tid; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        W.state[slots[q]] = 0;
+        W.active[slots[q]] = 0;
+    }
+}
+
+struct Layout2 {
+    Layout base;
+    size_t llr, syn, conv, iters, state, total;
+};
+
+Layout2 pool_layout(const qcldpc_code *code, int S, int fmt) {
+    Layout2 o;
+    o.base = layout_of(code->tab, S, false, fmt);
+    size_t off = o.base.total;
+    auto take = [&](size_t bytes) {
+        size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t words_m = (size_t)((code->m + 31) / 32);
+    o.llr = take(sizeof(float) * (size_t)S * (size_t)code->n);
+    o.syn = take(sizeof(uint32_t) * (size_t)S * words_m);
+    o.conv = take(sizeof(int32_t) * S);
+    o.iters = take(sizeof(int32_t) * S);
+    o.state = take(sizeof(int32_t) * S);
+    o.total = off;
+    return o;
+}
+
+constexpr int kPoolGraphs = 4;
+
+}  // namespace
+
+struct qcldpc_pool {
+    qcldpc_code *code;
+    Work w;
+    int n_slots;
+    struct StepGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int passes = 0;
+    } graphs[kPoolGraphs];
+    int next_graph = 0;
+};
+
+namespace {
+
+// Append n_passes iteration passes of one pool to graph g after node `dep`
+// (nullptr: a root chain). Returns the last node.
+cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes,
+                            cudaGraphNode_t *last) {
+    const Table &T = pool->code->tab;
+    const int F = pool->n_slots;
+    Table tcopy = T;
+    Work wcopy = pool->w;
+    void *args[] = {&tcopy, &wcopy};
+    cudaGraphConditionalHandle none = 0;
+    void *ctrl_args[] = {&wcopy, &none};
+    const CnLaunch cl = cn_launch(T, F, pool->w.fmt);
+    cudaGraphNode_t prev = nullptr;
+    cudaError_t err = cudaSuccess;
+    for (int i = 0; i < n_passes && err == cudaSuccess; i++) {
+        cudaGraphNode_t a, b, c;
+        err = add_kernel(&a, g, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, dim3(kThreads),
+                         args, cl.smem);
+        if (err == cudaSuccess)
+            err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),
+                             ctrl_args);
+        if (err == cudaSuccess)
+            err = add_kernel(&c, g, &b, 1, vn_kernel_for(pool->w.fmt), vn_grid(T, F), dim3(kThreads),
+                             args);
+        prev = c;
+    }
+    *last = prev;
+    return err;
+}
+
+// Graphs stepping several pools at once, cached by (pools, passes).
+struct MultiGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<qcldpc_pool *> pools;
+    int passes = 0;
+};
+constexpr int kMultiGraphs = 8;
+std::mutex g_multi_mu;
+MultiGraph g_multi[kMultiGraphs];
+int g_multi_next = 0;
+
+}  // namespace
+
+extern "C" size_t qcldpc_pool_workspace(const qcldpc_code *code, int n_slots,
+                                        const qcldpc_params *p) {
+    if (!code || n_slots < 1 || n_slots > 65535) return 0;
+    const int fmt = p ? p->msg_format : 0;
+    if (fmt < 0 || fmt > 2) return 0;
+    return pool_layout(code, n_slots, fmt).total;
+}
+
+extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int max_iter,
+                                  const qcldpc_params *p_in, void *workspace_dev,
+                                  size_t workspace_bytes, qcldpc_stream_t stream,
+                                  qcldpc_pool **out) {
+    using namespace qc;
+    if (!out) return fail(QCLDPC_E_INVAL, "pool_create: out is NULL");
+    *out = nullptr;
+    qcldpc_code *code = const_cast<qcldpc_code *>(code_c);
+    if (!code || !workspace_dev || n_slots < 1 || n_slots > 65535 || max_iter < 0)
+        return fail(QCLDPC_E_INVAL, "pool_create: bad argument");
+    qcldpc_params p;
+    if (p_in) p = *p_in;
+    else qcldpc_params_init(&p);
+    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format < 0 || p.msg_format > 2 ||
+        !(p.msg_step >= 0.0f) || p.soft_output)
+        return fail(QCLDPC_E_INVAL, "pool_create: unsupported option");
+    if (!aligned(workspace_dev, 256)) return fail(QCLDPC_E_ALIGN, "pool_create: workspace must be 256-byte aligned");
+    const Layout2 lo = pool_layout(code, n_slots, p.msg_format);
+    if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "pool_create: workspace too small");
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "pool_create: cudaGetDevice");
+    if (dev != code->device) return fail(QCLDPC_E_INVAL, "pool_create: current device differs from the code's device");
+    qcldpc_pool *pool = new (std::nothrow) qcldpc_pool();
+    if (!pool) return fail(QCLDPC_E_NOMEM, "pool_create: out of host memory");
+    char *base = static_cast<char *>(workspace_dev);
+    Work &w = pool->w;
+    std::memset(&w, 0, sizeof(w));
+    w.llr = reinterpret_cast<float *>(base + lo.llr);
+    w.syn = reinterpret_cast<uint32_t *>(base + lo.syn);
+    w.conv = reinterpret_cast<int32_t *>(base + lo.conv);
+    w.iters = reinterpret_cast<int32_t *>(base + lo.iters);
+    w.state = reinterpret_cast<int32_t *>(base + lo.state);
+    w.t = reinterpret_cast<int32_t *>(base + lo.base.t);
+    w.err = reinterpret_cast<int32_t *>(base + lo.base.err);
+    w.active = reinterpret_cast<int32_t *>(base + lo.base.active);
+    w.fail = reinterpret_cast<int32_t *>(base + lo.base.fail);
+    w.msg = base + lo.base.msg;
+    w.L = reinterpret_cast<float *>(base + lo.base.L);
+    w.phiq = reinterpret_cast<float *>(base + lo.base.phiq);
+    w.bits = reinterpret_cast<uint32_t *>(base + lo.base.bits);
+    w.n = code->n;
+    w.words_m = (code->m + 31) / 32;
+    w.words_k = (code->k + 31) / 32;
+    w.n_frames = n_slots;
+    w.max_iter = max_iter;
+    w.et_start = p.et_start;
+    w.ZW = (code->tab.Z + 31) / 32;
+    w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;
+    w.xmin = p.phi_floor * kLog2e;
+    w.fmt = p.msg_format;
+    if (w.fmt == 2) {
+        const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;
+        w.qstep = step * kLog2e;
+        w.qinv = 1.0f / w.qstep;
+    }
+    pool->code = code;
+    pool->n_slots = n_slots;
+    pool_reset_kernel<<<std::max(1, std::min(1024, (n_slots + kThreads - 1) / kThreads)), kThreads, 0,
+                        (cudaStream_t)stream>>>(w);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) {
+        delete pool;
+        return cuda_fail(err, "pool_create: launch");
+    }
+    clear_error();
+    *out = pool;
+    return QCLDPC_OK;
+}
+
+extern "C" void qcldpc_pool_destroy(qcldpc_pool *pool) {
+    if (!pool) return;
+    {
+        // drop cached multi-pool graphs that step this pool
+        std::lock_guard<std::mutex> lock(g_multi_mu);
+        for (auto &m : g_multi) {
+            if (m.exec && std::find(m.pools.begin(), m.pools.end(), pool) != m.pools.end()) {
+                cudaGraphExecDestroy(m.exec);
+                cudaGraphDestroy(m.graph);
+                m.exec = nullptr;
+                m.graph = nullptr;
+                m.pools.clear();
+            }
+        }
+    }
+    for (auto &g : pool->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (g.graph) cudaGraphDestroy(g.graph);
+    }
+    delete pool;
+}
+
+extern "C" int qcldpc_pool_state(const qcldpc_pool *pool, const int32_t **state_dev) {
+    if (!pool || !state_dev) return qc::fail(QCLDPC_E_INVAL, "pool_state: NULL argument");
+    *state_dev = pool->w.state;
+    return QCLDPC_OK;
+}
+
+extern "C" int qcldpc_pool_load(qcldpc_pool *pool, int n, const int32_t *slots_dev,
+                                const float *llr_dev, const uint32_t *syn_dev,
+                                qcldpc_stream_t stream) {
+    using namespace qc;
+    if (!pool || n < 0 || n > pool->n_slots) return fail(QCLDPC_E_INVAL, "pool_load: bad argument");
+    if (n == 0) return QCLDPC_OK;
+    if (!slots_dev || !llr_dev || !syn_dev) return fail(QCLDPC_E_INVAL, "pool_load: NULL buffer");
+    if (!aligned(slots_dev, 4) || !aligned(llr_dev, 4) || !aligned(syn_dev, 4))
+        return fail(QCLDPC_E_ALIGN, "pool_load: buffers must be 4-byte aligned");
+    std::lock_guard<std::mutex> lock(pool->code->mu);
+    pool_load_kernel<<<sm_count() * 4, kThreads, 0, (cudaStream_t)stream>>>(pool->code->tab, pool->w,
+                                                                         slots_dev, n, llr_dev, syn_dev);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "pool_load: launch");
+    return QCLDPC_OK;
+}
+
+extern "C" int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_passes,
+                                 qcldpc_stream_t stream) {
+    using namespace qc;
+    if (n_pools < 1 || !pools || n_passes < 1) return fail(QCLDPC_E_INVAL, "pools_step: bad argument");
+    for (int i = 0; i < n_pools; i++)
+        if (!pools[i]) return fail(QCLDPC_E_INVAL, "pools_step: NULL pool");
+    // A single pool caches its step graph; several pools build a fresh graph
+    // with one branch per pool (their passes run concurrently).
+    cudaError_t err;
+    if (n_pools == 1) {
+        qcldpc_pool *pool = pools[0];
+        std::lock_guard<std::mutex> lock(pool->code->mu);
+        qcldpc_pool::StepGraph *hit = nullptr;
+        for (auto &g : pool->graphs)
+            if (g.exec && g.passes == n_passes) hit = &g;
+        if (!hit) {
+            hit = &pool->graphs[pool->next_graph];
+            pool->next_graph = (pool->next_graph + 1) % kPoolGraphs;
+            if (hit->exec) cudaGraphExecDestroy(hit->exec);
+            if (hit->graph) cudaGraphDestroy(hit->graph);
+            hit->exec = nullptr;
+            hit->graph = nullptr;
+            if ((err = cudaGraphCreate(&hit->graph, 0)) != cudaSuccess) return cuda_fail(err, "pools_step: cudaGraphCreate");
+            cudaGraphNode_t last;
+            if ((err = add_pool_passes(hit->graph, pool, n_passes, &last)) != cudaSuccess)
+                return cuda_fail(err, "pools_step: add passes");
+            if ((err = cudaGraphInstantiate(&hit->exec, hit->graph, 0)) != cudaSuccess) {
+                hit->exec = nullptr;
+                return cuda_fail(err, "pools_step: cudaGraphInstantiate");
+            }
+            hit->passes = n_passes;
+        }
+        if ((err = cudaGraphLaunch(hit->exec, (cudaStream_t)stream)) != cudaSuccess)
+            return cuda_fail(err, "pools_step: cudaGraphLaunch");
+        return QCLDPC_OK;
+    }
+    std::lock_guard<std::mutex> lock(g_multi_mu);
+    MultiGraph *hit = nullptr;
+    for (auto &m : g_multi)
+        if (m.exec && m.passes == n_passes && m.pools.size() == (size_t)n_pools &&
+            std::equal(m.pools.begin(), m.pools.end(), pools))
+            hit = &m;
+    if (!hit) {
+        hit = &g_multi[g_multi_next];
+        g_multi_next = (g_multi_next + 1) % kMultiGraphs;
+        if (hit->exec) cudaGraphExecDestroy(hit->exec);
+        if (hit->graph) cudaGraphDestroy(hit->graph);
+        hit->exec = nullptr;
+        hit->graph = nullptr;
+        if ((err = cudaGraphCreate(&hit->graph, 0)) != cudaSuccess)
+            return cuda_fail(err, "pools_step: cudaGraphCreate");
+        err = cudaSuccess;
+        for (int i = 0; i < n_pools && err == cudaSuccess; i++) {
+            cudaGraphNode_t last;
+            err = add_pool_passes(hit->graph, pools[i], n_passes, &last);
+        }
+        if (err == cudaSuccess) err = cudaGraphInstantiate(&hit->exec, hit->graph, 0);
+        if (err != cudaSuccess) {
+            hit->exec = nullptr;
+            return cuda_fail(err, "pools_step: build graph");
+        }
+        hit->pools.assign(pools, pools + n_pools);
+        hit->passes = n_passes;
+    }
+    if ((err = cudaGraphLaunch(hit->exec, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(err, "pools_step: cudaGraphLaunch");
+    return QCLDPC_OK;
+}
+
+extern "C" int qcldpc_pool_step(qcldpc_pool *pool, int n_passes, qcldpc_stream_t stream) {
+    return qcldpc_pools_step(1, &pool, n_passes, stream);
+}
+
+extern "C" int qcldpc_pool_collect(qcldpc_pool *pool, int n, const int32_t *slots_dev,
+                                   uint32_t *key_bits_dev, int32_t *converged_dev,
+                                   int32_t *iters_dev, qcldpc_stream_t stream) {
+    using namespace qc;
+    if (!pool || n < 0 || n > pool->n_slots) return fail(QCLDPC_E_INVAL, "pool_collect: bad argument");
+    if (n == 0) return QCLDPC_OK;
+    if (!slots_dev || !key_bits_dev || !converged_dev || !iters_dev)
+        return fail(QCLDPC_E_INVAL, "pool_collect: NULL buffer");
+    std::lock_guard<std::mutex> lock(pool->code->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    pool_collect_kernel<<<sm_count() * 2, kThreads, 0, st>>>(pool->code->tab, pool->w, slots_dev, n,
+                                                            key_bits_dev, converged_dev, iters_dev);
+    pool_free_kernel<<<1, kThreads, 0, st>>>(pool->w, slots_dev, n);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "pool_collect: launch");
     return QCLDPC_OK;
 }
 

@@ -106,6 +106,66 @@ __global__ void __launch_bounds__(256) llr8_kernel(const float4 *__restrict__ x,
     }
 }
 
+// d in {1, 2, 4}: reals, complex numbers (Cayley-Dickson doubling of the
+// reals) and quaternions (Hamilton's rule), one thread per block of d.
+// Bob: M = U Y. Alice: Q = (M conj(X)) * 2 snr / d (sigma_N^2 = d sigma_Z^2 /
+// |X|^2, so |X|^2 cancels as in the 8-D map).
+template <int D>
+__global__ void __launch_bounds__(256) bob_d_kernel(const float *__restrict__ y,
+                                                    const uint32_t *__restrict__ bits,
+                                                    float *__restrict__ out, int64_t n_blocks) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = b * D;
+        float u[D], yy[D];
+#pragma unroll
+        for (int j = 0; j < D; j++) {
+            const int64_t v = v0 + j;
+            u[j] = ((__ldg(bits + (v >> 5)) >> (v & 31)) & 1u) ? -1.0f : 1.0f;
+            yy[j] = __ldg(y + v);
+        }
+        if constexpr (D == 1) {
+            out[v0] = u[0] * yy[0];
+        } else if constexpr (D == 2) {  // (a + ib)(c + id)
+            out[v0] = u[0] * yy[0] - u[1] * yy[1];
+            out[v0 + 1] = u[0] * yy[1] + u[1] * yy[0];
+        } else {
+            const Quat r = qmul(Quat{u[0], u[1], u[2], u[3]}, Quat{yy[0], yy[1], yy[2], yy[3]});
+            out[v0] = r.w;
+            out[v0 + 1] = r.x;
+            out[v0 + 2] = r.y;
+            out[v0 + 3] = r.z;
+        }
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) llr_d_kernel(const float *__restrict__ x,
+                                                    const float *__restrict__ m,
+                                                    float *__restrict__ llr, float scale,
+                                                    int64_t n_blocks) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_blocks;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v0 = b * D;
+        if constexpr (D == 1) {
+            llr[v0] = __ldg(m + v0) * __ldg(x + v0) * scale;
+        } else if constexpr (D == 2) {  // M conj(X) = (a + ib)(c - id)
+            const float a = __ldg(m + v0), bb = __ldg(m + v0 + 1);
+            const float c = __ldg(x + v0), d = __ldg(x + v0 + 1);
+            llr[v0] = (a * c + bb * d) * scale;
+            llr[v0 + 1] = (bb * c - a * d) * scale;
+        } else {
+            const Quat mq{__ldg(m + v0), __ldg(m + v0 + 1), __ldg(m + v0 + 2), __ldg(m + v0 + 3)};
+            const Quat xq{__ldg(x + v0), __ldg(x + v0 + 1), __ldg(x + v0 + 2), __ldg(x + v0 + 3)};
+            const Quat r = qmul(mq, qconj(xq));
+            llr[v0] = r.w * scale;
+            llr[v0 + 1] = r.x * scale;
+            llr[v0 + 2] = r.y * scale;
+            llr[v0 + 3] = r.z * scale;
+        }
+    }
+}
+
 int stream_grid(int64_t n_blocks) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -167,5 +227,45 @@ extern "C" int qcldpc_llr_8d(const float *x_dev, const float *m_dev, int64_t n, 
         reinterpret_cast<float4 *>(llr_dev), snr * 0.25f, nb);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "llr_8d: launch");
+    return QCLDPC_OK;
+}
+
+extern "C" int qcldpc_bob_message(int d, const float *y_dev, const uint32_t *bits_dev, int64_t n,
+                                  float *m_dev, qcldpc_stream_t stream) {
+    using namespace qc;
+    if (d == 8) return qcldpc_bob_message_8d(y_dev, bits_dev, n, m_dev, stream);
+    if ((d != 1 && d != 2 && d != 4) || !y_dev || !bits_dev || !m_dev || n < 0 || n % d != 0)
+        return fail(QCLDPC_E_INVAL, "bob_message: d must be 1, 2, 4 or 8 and n a multiple of d");
+    if (!aligned(y_dev, 4) || !aligned(m_dev, 4) || !aligned(bits_dev, 4))
+        return fail(QCLDPC_E_ALIGN, "bob_message: buffers must be 4-byte aligned");
+    if (n == 0) return QCLDPC_OK;
+    const int64_t nb = n / d;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d == 1) bob_d_kernel<1><<<stream_grid(nb), 256, 0, st>>>(y_dev, bits_dev, m_dev, nb);
+    else if (d == 2) bob_d_kernel<2><<<stream_grid(nb), 256, 0, st>>>(y_dev, bits_dev, m_dev, nb);
+    else bob_d_kernel<4><<<stream_grid(nb), 256, 0, st>>>(y_dev, bits_dev, m_dev, nb);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "bob_message: launch");
+    return QCLDPC_OK;
+}
+
+extern "C" int qcldpc_llr(int d, const float *x_dev, const float *m_dev, int64_t n, float snr,
+                          float *llr_dev, qcldpc_stream_t stream) {
+    using namespace qc;
+    if (d == 8) return qcldpc_llr_8d(x_dev, m_dev, n, snr, llr_dev, stream);
+    if ((d != 1 && d != 2 && d != 4) || !x_dev || !m_dev || !llr_dev || n < 0 || n % d != 0 ||
+        !(snr > 0.0f))
+        return fail(QCLDPC_E_INVAL, "llr: d must be 1, 2, 4 or 8, n a multiple of d, snr > 0");
+    if (!aligned(x_dev, 4) || !aligned(m_dev, 4) || !aligned(llr_dev, 4))
+        return fail(QCLDPC_E_ALIGN, "llr: buffers must be 4-byte aligned");
+    if (n == 0) return QCLDPC_OK;
+    const int64_t nb = n / d;
+    const float scale = 2.0f * snr / (float)d;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d == 1) llr_d_kernel<1><<<stream_grid(nb), 256, 0, st>>>(x_dev, m_dev, llr_dev, scale, nb);
+    else if (d == 2) llr_d_kernel<2><<<stream_grid(nb), 256, 0, st>>>(x_dev, m_dev, llr_dev, scale, nb);
+    else llr_d_kernel<4><<<stream_grid(nb), 256, 0, st>>>(x_dev, m_dev, llr_dev, scale, nb);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "llr: launch");
     return QCLDPC_OK;
 }

@@ -26,8 +26,11 @@ STATUS = {
 EXPORTED = [
     "qcldpc_create_code", "qcldpc_destroy_code", "qcldpc_code_info",
     "qcldpc_syndrome", "qcldpc_bob_message_8d", "qcldpc_llr_8d",
+    "qcldpc_bob_message", "qcldpc_llr",
     "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
     "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc",
+    "qcldpc_pool_workspace", "qcldpc_pool_create", "qcldpc_pool_destroy", "qcldpc_pool_state",
+    "qcldpc_pool_load", "qcldpc_pool_step", "qcldpc_pools_step", "qcldpc_pool_collect",
     "qcldpc_last_error",
 ]
 
@@ -84,6 +87,10 @@ def load(build_if_missing: bool = True):
         lib.qcldpc_bob_message_8d.restype = i32
         lib.qcldpc_llr_8d.argtypes = [vp, vp, i64, ctypes.c_float, vp, vp]
         lib.qcldpc_llr_8d.restype = i32
+        lib.qcldpc_bob_message.argtypes = [i32, vp, vp, i64, vp, vp]
+        lib.qcldpc_bob_message.restype = i32
+        lib.qcldpc_llr.argtypes = [i32, vp, vp, i64, ctypes.c_float, vp, vp]
+        lib.qcldpc_llr.restype = i32
         lib.qcldpc_params_init.argtypes = [ctypes.POINTER(qcldpc_params)]
         lib.qcldpc_params_init.restype = None
         lib.qcldpc_decode_workspace.argtypes = [vp, i32, ctypes.POINTER(qcldpc_params)]
@@ -100,6 +107,23 @@ def load(build_if_missing: bool = True):
         lib.qcldpc_decode_noalloc.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
                                               vp, vp, vp, vp]
         lib.qcldpc_decode_noalloc.restype = i32
+        lib.qcldpc_pool_workspace.argtypes = [vp, i32, ctypes.POINTER(qcldpc_params)]
+        lib.qcldpc_pool_workspace.restype = sz
+        lib.qcldpc_pool_create.argtypes = [vp, i32, i32, ctypes.POINTER(qcldpc_params), vp, sz, vp,
+                                           ctypes.POINTER(vp)]
+        lib.qcldpc_pool_create.restype = i32
+        lib.qcldpc_pool_destroy.argtypes = [vp]
+        lib.qcldpc_pool_destroy.restype = None
+        lib.qcldpc_pool_state.argtypes = [vp, ctypes.POINTER(vp)]
+        lib.qcldpc_pool_state.restype = i32
+        lib.qcldpc_pool_load.argtypes = [vp, i32, vp, vp, vp, vp]
+        lib.qcldpc_pool_load.restype = i32
+        lib.qcldpc_pool_step.argtypes = [vp, i32, vp]
+        lib.qcldpc_pool_step.restype = i32
+        lib.qcldpc_pools_step.argtypes = [i32, vp, i32, vp]
+        lib.qcldpc_pools_step.restype = i32
+        lib.qcldpc_pool_collect.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+        lib.qcldpc_pool_collect.restype = i32
         lib.qcldpc_last_error.argtypes = []
         lib.qcldpc_last_error.restype = ctypes.c_char_p
         _lib = lib
@@ -212,6 +236,18 @@ def qcldpc_llr_8d(x_dev, m_dev, n: int, snr: float, llr_dev, stream=None):
     _check(st, "qcldpc_llr_8d")
 
 
+def qcldpc_bob_message(d: int, y_dev, bits_dev, n: int, m_dev, stream=None):
+    st = load().qcldpc_bob_message(int(d), _dev(y_dev, 4, "y_dev"), _dev(bits_dev, 4, "bits_dev"),
+                                   int(n), _dev(m_dev, 4, "m_dev"), _stream(stream))
+    _check(st, "qcldpc_bob_message")
+
+
+def qcldpc_llr(d: int, x_dev, m_dev, n: int, snr: float, llr_dev, stream=None):
+    st = load().qcldpc_llr(int(d), _dev(x_dev, 4, "x_dev"), _dev(m_dev, 4, "m_dev"), int(n),
+                           float(snr), _dev(llr_dev, 4, "llr_dev"), _stream(stream))
+    _check(st, "qcldpc_llr")
+
+
 def qcldpc_decode_workspace(code: Code, n_frames: int, params: qcldpc_params | None = None) -> int:
     p = ctypes.byref(params) if params is not None else None
     return int(load().qcldpc_decode_workspace(code.handle, int(n_frames), p))
@@ -303,3 +339,75 @@ class Decoder:
             qcldpc_decode(self.code, llr_dev, syn_dev, self.n_frames, max_iter, self.params,
                           self.keys, self.converged, self.iters, self.workspace,
                           self.ws_bytes, stream)
+
+
+# ---------------------------------------------------------------- pools
+
+def qcldpc_pool_workspace(code: Code, n_slots: int, params: qcldpc_params | None = None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    return int(load().qcldpc_pool_workspace(code.handle, int(n_slots), p))
+
+
+class Pool:
+    """Owning wrapper of a qcldpc_pool: n_slots frame slots of one code.
+
+    Holds its workspace tensor; ``state`` is a view of the device slot states
+    (0 free, 1 running, 2 stopped).
+    """
+
+    def __init__(self, code: Code, n_slots: int, max_iter: int,
+                 params: qcldpc_params | None = None, stream=None, device=None):
+        import torch
+        self.code, self.n_slots, self.max_iter = code, int(n_slots), int(max_iter)
+        self.params = params if params is not None else qcldpc_params_init()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.ws_bytes = qcldpc_pool_workspace(code, self.n_slots, self.params)
+        if self.ws_bytes == 0:
+            raise QcldpcError(-1, "qcldpc_pool_workspace", "invalid arguments")
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        h = ctypes.c_void_p()
+        st = load().qcldpc_pool_create(code.handle, self.n_slots, self.max_iter,
+                                       ctypes.byref(self.params), _dev(self.workspace, None, "ws"),
+                                       self.ws_bytes, _stream(stream), ctypes.byref(h))
+        _check(st, "qcldpc_pool_create")
+        self._h = h
+        ptr = ctypes.c_void_p()
+        _check(load().qcldpc_pool_state(self._h, ctypes.byref(ptr)), "qcldpc_pool_state")
+        off = ptr.value - self.workspace.data_ptr()
+        self.state = self.workspace[off: off + 4 * self.n_slots].view(torch.int32)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h is not None and _lib is not None:
+            _lib.qcldpc_pool_destroy(h)
+
+
+def qcldpc_pool_load(pool: Pool, n: int, slots_dev, llr_dev, syn_dev, stream=None):
+    st = load().qcldpc_pool_load(pool.handle, int(n), _dev(slots_dev, 4, "slots_dev"),
+                                 _dev(llr_dev, 4, "llr_dev"), _dev(syn_dev, 4, "syn_dev"),
+                                 _stream(stream))
+    _check(st, "qcldpc_pool_load")
+
+
+def qcldpc_pool_step(pool: Pool, n_passes: int, stream=None):
+    _check(load().qcldpc_pool_step(pool.handle, int(n_passes), _stream(stream)), "qcldpc_pool_step")
+
+
+def qcldpc_pools_step(pools, n_passes: int, stream=None):
+    arr = (ctypes.c_void_p * len(pools))(*[p.handle.value for p in pools])
+    st = load().qcldpc_pools_step(len(pools), ctypes.cast(arr, ctypes.c_void_p), int(n_passes),
+                                  _stream(stream))
+    _check(st, "qcldpc_pools_step")
+
+
+def qcldpc_pool_collect(pool: Pool, n: int, slots_dev, key_bits_dev, converged_dev, iters_dev,
+                        stream=None):
+    st = load().qcldpc_pool_collect(pool.handle, int(n), _dev(slots_dev, 4, "slots_dev"),
+                                    _dev(key_bits_dev, 4, "key_bits_dev"),
+                                    _dev(converged_dev, 4, "converged_dev"),
+                                    _dev(iters_dev, 4, "iters_dev"), _stream(stream))
+    _check(st, "qcldpc_pool_collect")

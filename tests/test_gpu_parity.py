@@ -162,6 +162,28 @@ def test_bob_message_and_llr_8d(Z, F, snr):
     assert np.all(np.abs(got - ref) <= tol)
 
 
+@pytest.mark.parametrize("d", [1, 2, 4, 8])
+def test_bob_message_and_llr_all_dimensions(d):
+    """The d-dimensional maps of Sec. II-C against the oracle (Z=64, 2 frames)."""
+    fr = make_frames(synth.rate002_code(64), 0.1, 2, d=d)
+    n = fr.x32.size
+    m_gpu = torch.empty(n, dtype=torch.float32, device="cuda")
+    q.qcldpc_bob_message(d, dev(fr.y32.reshape(-1)),
+                         dev(packed(fr.bits.reshape(1, -1)).view(np.int32).reshape(-1)), n, m_gpu)
+    llr = torch.empty(n, dtype=torch.float32, device="cuda")
+    q.qcldpc_llr(d, dev(fr.x32.reshape(-1)), dev(fr.m32.reshape(-1)), n, fr.snr, llr)
+    torch.cuda.synchronize()
+    m_ref = np.concatenate([oracle.bob_message(fr.y32[f].astype(np.float64), fr.bits[f], d=d)
+                            for f in range(fr.F)])
+    yb = np.repeat(np.linalg.norm(fr.y32.reshape(-1, d).astype(np.float64), axis=1), d)
+    assert np.all(np.abs(m_gpu.cpu().numpy() - m_ref) <= 16 * U32 * np.sqrt(d) * yb + 1e-30)
+    ref = fr.q64.reshape(-1)
+    xb = np.linalg.norm(fr.x32.reshape(-1, d).astype(np.float64), axis=1)
+    mb = np.linalg.norm(fr.m32.reshape(-1, d).astype(np.float64), axis=1)
+    tol = np.repeat(16 * U32 * xb * mb * 2 * fr.snr / d, d) + 2 * U32 * np.abs(ref) + 1e-30
+    assert np.all(np.abs(llr.cpu().numpy().astype(np.float64) - ref) <= tol)
+
+
 def test_llr_rejects_bad_length_and_alignment():
     x = torch.zeros(24, device="cuda")
     with pytest.raises(q.QcldpcError, match="INVAL"):
