@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--reps", type=int, default=20, help="replays per pass for the roofline")
     ap.add_argument("--launch-mode", choices=["graph", "stream"], default="graph",
                     help="stream: host-enqueued passes, for profilers only (not a bench number)")
+    ap.add_argument("--msg-format", choices=["fp32", "fp16", "int8"], default="fp32",
+                    help="storage of edge messages (arithmetic stays FP32)")
     return ap.parse_args()
 
 
@@ -161,7 +163,7 @@ class ClockSampler:
 
 # ------------------------------------------------------- algorithmic bytes
 
-def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int):
+def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_bytes: int = 4):
     """Bytes one frame's check-node / variable-node pass must move (FP32).
 
     Check pass: read and write every heavy message (n_h Z floats each way),
@@ -171,8 +173,8 @@ def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int):
     Variable pass: read every heavy message once, the heavy channel LLRs, and
     write the heavy posteriors.
     """
-    cn = 4 * (2 * n_h * Z + n_d1 * Z + n_hcols * Z) + (mb * Z + 2 * n_d1 * Z) / 8
-    vn = 4 * (n_h * Z + 2 * n_hcols * Z)
+    cn = 2 * msg_bytes * n_h * Z + 4 * (n_d1 * Z + n_hcols * Z) + (mb * Z + 2 * n_d1 * Z) / 8
+    vn = msg_bytes * n_h * Z + 4 * 2 * n_hcols * Z
     return cn, vn
 
 
@@ -191,19 +193,21 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
-    None when the kernel source changed since it was captured."""
+def ncu_traffic(pass_name: str, msg_format: str, frames: int):
+    """(kernel name, per-launch DRAM bytes) of a decoder pass from the
+    committed ncu summary, or (None, None) when the kernel source changed
+    since the capture or the capture was of another configuration."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
-        return None
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != source_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+        return None, None
+    e = d.get(pass_name)
+    if (not e or e.get("source_hash") != source_hash() or e.get("msg_format", "fp32") != msg_format
+            or e.get("frames") != frames):
+        return None, None
+    return e.get("kernel"), e.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -280,7 +284,8 @@ def run_ours(args, world, rank, local):
     code = q.create_code_from(d)
     n, k, F, B = code.n, code.k, args.frames, args.batches
     wm, wk = (code.m + 31) // 32, (k + 31) // 32
-    params = q.qcldpc_params_init(launch_mode=1 if args.launch_mode == "stream" else 0)
+    params = q.qcldpc_params_init(launch_mode=1 if args.launch_mode == "stream" else 0,
+                                  msg_format={"fp32": 0, "fp16": 1, "int8": 2}[args.msg_format])
 
     # --- seeded inputs, resident in HBM before timing
     host = []
@@ -410,13 +415,13 @@ def run_ours(args, world, rank, local):
     heavy = col_count != 1
     cn_b, vn_b = pass_bytes(args.Z, n_h=int(heavy[d["col"]].sum()),
                             n_d1=int((~heavy[d["col"]]).sum()), n_hcols=int(heavy.sum()),
-                            mb=d["mb"])
+                            mb=d["mb"], msg_bytes={"fp32": 4, "fp16": 2, "int8": 1}[args.msg_format])
     peaks, peak_kind = measured_peaks()
-    dom, dom_ms, dom_bytes = (("cn_kernel", cn_ms, cn_b * F) if cn_ms >= vn_ms
-                              else ("vn_kernel", vn_ms, vn_b * F))
+    dom, dom_ms, dom_bytes = (("check_pass", cn_ms, cn_b * F) if cn_ms >= vn_ms
+                              else ("variable_pass", vn_ms, vn_b * F))
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    traffic = ncu_traffic(dom)
+    kname, traffic = ncu_traffic(dom, args.msg_format, F)
     iter_ms = cn_ms + vn_ms
     if rank != 0:
         if world > 1:
@@ -440,6 +445,7 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "msg_format": args.msg_format,
         "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "k": k, "snr": args.snr,
                    "frames_per_step": F, "distinct_frames": frames_total,
                    "max_iter": args.max_iter, "stop_test": "after every iteration",
@@ -454,7 +460,7 @@ def run_ours(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname or dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "cn_ms": cn_ms, "vn_ms": vn_ms,

@@ -159,6 +159,19 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
     }
     T.row_ptr[mb] = (uint16_t)pos;
     T.max_row_deg = max_deg;
+    // Check-node blocks visit rows in this order: rows of one shape (heavy
+    // and degree-1 counts) are adjacent, so blocks resident together tend to
+    // run the same code.
+    {
+        std::vector<int> order(mb);
+        for (int r = 0; r < mb; r++) order[r] = r;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            const int da = T.row_ptr[a + 1] - T.row_ptr[a], db = T.row_ptr[b + 1] - T.row_ptr[b];
+            if (T.row_nh[a] != T.row_nh[b]) return T.row_nh[a] < T.row_nh[b];
+            return da < db;
+        });
+        for (int r = 0; r < mb; r++) T.row_order[r] = (uint8_t)order[r];
+    }
     const int ZW = (Z + 31) / 32;
     for (int q = 0; q < pos; q++) {
         const RowEnt &e = T.rows[q];

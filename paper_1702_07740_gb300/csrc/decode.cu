@@ -88,9 +88,13 @@ constexpr int kGraphCacheSize = 8;
 #define QCLDPC_CN_TMA 1
 #endif
 #ifndef QCLDPC_CN_TVPT
-#define QCLDPC_CN_TVPT 6
+#define QCLDPC_CN_TVPT 4
 #endif
 constexpr int kTmaVpt = QCLDPC_CN_TVPT;
+#ifndef QCLDPC_CN_UNROLL
+#define QCLDPC_CN_UNROLL 4
+#endif
+constexpr int kCnUnroll = QCLDPC_CN_UNROLL;
 constexpr int kTile = kThreads * kTmaVpt;      // checks per block
 constexpr int kStage = kTile + 4;              // staged floats per row (16-byte realignment)
 constexpr int kStageWords = kTile / 32 + 4;    // staged decision words per row
@@ -678,7 +682,7 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     const bool staged = stage_wait(bar, W);
     bool bad = false;
     if (staged) {
-#pragma unroll
+#pragma unroll kCnUnroll
         for (int c = 0; c < kTmaVpt; c++) {
             const int i = i0 + c * kThreads + tid;
             const bool valid = i < Z;
@@ -792,7 +796,7 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const
                                                          const __grid_constant__ Work W) {
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
-    const int r = blockIdx.y;
+    const int r = T.row_order[blockIdx.y];
     const int t = W.t[f];
     const int mode = t > W.max_iter ? kTestOnly
                      : t == 1       ? kFirst
@@ -825,7 +829,7 @@ __global__ void __launch_bounds__(kThreads) cn_tma_kernel(const __grid_constant_
     extern __shared__ __align__(128) unsigned char smem[];
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
-    const int r = blockIdx.y;
+    const int r = T.row_order[blockIdx.y];
     const int t = W.t[f];
     const int mode = t > W.max_iter ? kTestOnly
                      : t == 1       ? kFirst
@@ -859,7 +863,6 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     const bool failed = *W.err != 0;  // a staged copy never completed: stop, flag -1
-    int mine = 0;
     for (int f = threadIdx.x; f < W.n_frames; f += blockDim.x) {
         if (W.active[f]) {
             const int t = W.t[f];
@@ -878,18 +881,20 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
             } else {
                 stop = false;
                 W.t[f] = t + 1;
-                mine = 1;
             }
             if (stop) {
                 W.active[f] = 0;
                 if (W.state) W.state[f] = 2;
+            } else {
+                any = 1;
             }
         }
         W.fail[f] = 0;
     }
-    if (mine) atomicOr(&any, 1);
-    __syncthreads();
-    if (kInGraph && threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    if (kInGraph) {
+        __syncthreads();
+        if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+    }
 }
 
 // Variable-node pass: L_v = Q_v + sum_c m_cv for every heavy variable node.
@@ -1150,10 +1155,30 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
 }
 
+// Loop body of the decode graph: check pass -> control -> variable pass.
+cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
+                          cudaGraphConditionalHandle handle) {
+    const int F = w0.n_frames;
+    Table tcopy = T;
+    Work wcopy = w0;
+    void *args[] = {&tcopy, &wcopy};
+    cudaGraphNode_t n_cn, n_ctrl, n_vn;
+    const CnLaunch cl = cn_launch(T, F, w0.fmt);
+    cudaError_t err;
+    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, dim3(kThreads), args,
+                          cl.smem)) != cudaSuccess)
+        return err;
+    void *ctrl_args[] = {&wcopy, &handle};
+    if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
+                          dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
+        return err;
+    return add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
+                      dim3(kThreads), args);
+}
+
 // Build and instantiate the decode graph for one argument set.
 int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
     const Table &T = code->tab;
-    const int F = w0.n_frames;
     cudaError_t err;
     cudaGraph_t g = nullptr;
     if ((err = cudaGraphCreate(&g, 0)) != cudaSuccess) return qc::cuda_fail(err, "decode: cudaGraphCreate");
@@ -1178,18 +1203,8 @@ int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
     if ((err = cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add conditional node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    cudaGraphNode_t n_cn, n_ctrl, n_vn;
-    const CnLaunch cl = cn_launch(T, F, w0.fmt);
-    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, dim3(kThreads), args,
-                          cl.smem)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode: add check-node kernel");
-    void *ctrl_args[] = {&wcopy, &handle};
-    if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
-                          dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode: add control kernel");
-    if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
-                          dim3(kThreads), args)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode: add variable-node kernel");
+    if ((err = add_loop_body(body, T, w0, handle)) != cudaSuccess)
+        return qc::cuda_fail(err, "decode: add loop body");
     if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks),
                           dim3(kThreads), args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add output kernel");

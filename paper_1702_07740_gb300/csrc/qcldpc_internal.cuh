@@ -47,6 +47,7 @@ struct Table {
     int32_t pad_;
     uint16_t row_ptr[kMaxRows + 1];     // into rows[]
     uint8_t row_nh[kMaxRows];           // heavy entries of the row
+    uint8_t row_order[kMaxRows];        // rows sorted by shape (check-node grid order)
     uint16_t col_ptr[kMaxHeavyCols + 1];  // into cols[]
     int16_t hcol_base[kMaxHeavyCols];   // base column of each heavy slot
     int16_t col_kind[kMaxCols];         // >= 0 heavy slot; <= -2: d1 id = -kind-2
