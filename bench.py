@@ -61,6 +61,18 @@ def parse_args():
                     help="stream: host-enqueued passes, for profilers only (not a bench number)")
     ap.add_argument("--msg-format", choices=["fp32", "fp16", "int8"], default="fp32",
                     help="storage of edge messages (arithmetic stays FP32)")
+    ap.add_argument("--study", choices=["fer", "batch", "serve"], default=None,
+                    help="instead of the throughput line: FER per message format (fer), a "
+                         "mixed-rate 256-frame batch (batch) or a serving-load sweep (serve)")
+    ap.add_argument("--study-frames", type=int, default=2000, help="fer: frames per SNR")
+    ap.add_argument("--study-snrs", default="0.13,0.16", help="fer: SNRs of the rate-0.02 code")
+    ap.add_argument("--mix-snrs", default="0.16,0.5,1.0",
+                    help="batch/serve: SNR of the rate 0.02 / 0.05 / 0.10 codes")
+    ap.add_argument("--mix-frames", type=int, default=256, help="batch: frames in the mix")
+    ap.add_argument("--loads", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
+                    help="serve: offered load as a fraction of the measured batched capacity")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="serve: arrival window per load point")
     return ap.parse_args()
 
 
@@ -477,6 +489,10 @@ def run_ours(args, world, rank, local):
 def main():
     args = parse_args()
     world, rank, local = dist_env()
+    if args.study:
+        import bench_studies
+        bench_studies.run(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

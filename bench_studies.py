@@ -1,0 +1,404 @@
+"""Studies beside bench.py's throughput line (``bench.py --study ...``).
+
+* ``fer``: the same seeded n = 10^6 frames decoded with edge messages stored
+  in FP32, FP16 and int8 (arithmetic FP32); per format the frame error rate
+  with its Wilson 95 % interval, the paired difference to FP32 with its 95 %
+  interval, mean iterations and decoded Mbit/s.
+* ``batch``: 256 frames mixing three rates (0.02 at n = 10^6, 0.05 at
+  n = 5*10^5, 0.10 at n = 10^5) decoded together by frame pools stepped in one
+  graph launch (FP16 and FP32 messages), against the plain FP32 decoder run
+  one frame at a time and one code at a time.
+* ``serve``: Poisson arrivals of frames of the same mix into the
+  continuous-batching server (FP16 messages) at offered loads from 10 % to
+  120 % of its measured capacity; p50/p99 frame latency and served Mbit/s,
+  next to a first-in-first-out server that decodes one frame at a time with
+  the plain FP32 decoder on the same arrivals.
+
+Frames are seeded synthetic channel draws made on the device with torch's
+Philox generator (x ~ N(0,1), y = x + N(0, 1/SNR), uniform bits); Bob's
+message, the syndrome and Alice's LLRs then come from the library's own
+kernels. Every variant of a study decodes the same frames, so differences in
+frame errors are paired. A frame error is a key that differs from Bob's first
+k bits (converged or not).
+"""
+from __future__ import annotations
+
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+import synth
+from bench import wilson
+from paper_1702_07740_gb300 import qcldpc as q
+from paper_1702_07740_gb300 import serve
+
+MIX = (("r002", synth.rate002_code, 20000),
+       ("r005", synth.rate005_code, 25000),
+       ("r010", synth.rate010_code, 10000))
+FMT = {"fp32": 0, "fp16": 1, "int8": 2}
+
+
+# ------------------------------------------------------------------ frames
+
+def pack_dev(bits: torch.Tensor) -> torch.Tensor:
+    """0/1 int32 [F, n] (n a multiple of 32) -> int32 [F, n/32], LSB first."""
+    F, n = bits.shape
+    sh = torch.arange(32, device=bits.device, dtype=torch.int64)
+    w = (bits.view(F, n // 32, 32).to(torch.int64) << sh).sum(-1)
+    w = torch.where(w >= 2 ** 31, w - 2 ** 32, w)
+    return w.to(torch.int32)
+
+
+def make_frames(code, F: int, snr: float, seed: int):
+    """(llr float[F n], syndrome int32[F ceil(m/32)], Bob's key int32[F, ceil(k/32)])."""
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    n, k, m = code.n, code.k, code.m
+    wm, wk = (m + 31) // 32, (k + 31) // 32
+    x = torch.randn(F * n, generator=g, device=dev)
+    y = x + torch.randn(F * n, generator=g, device=dev) * (1.0 / snr) ** 0.5
+    words = pack_dev(torch.randint(0, 2, (F, n), generator=g, device=dev, dtype=torch.int32))
+    msg = torch.empty_like(x)
+    q.qcldpc_bob_message_8d(y, words.view(-1), F * n, msg)
+    del y
+    syn = torch.empty(F * wm, dtype=torch.int32, device=dev)
+    q.qcldpc_syndrome(code, words.view(-1), syn, F)
+    llr = torch.empty_like(x)
+    q.qcldpc_llr_8d(x, msg, F * n, snr, llr)
+    key = words[:, :wk].clone()
+    if k % 32:
+        key[:, -1] &= (1 << (k % 32)) - 1
+    return llr, syn, key
+
+
+def paired(e_ref: np.ndarray, e: np.ndarray) -> dict:
+    """Paired FER difference (e - e_ref) with a 95 % normal interval."""
+    N = len(e)
+    b = int(((e_ref == 0) & (e == 1)).sum())
+    c = int(((e_ref == 1) & (e == 0)).sum())
+    d = (b - c) / N
+    se = math.sqrt(max(b + c - (b - c) ** 2 / N, 0.0)) / N
+    return {"only_this_fails": b, "only_ref_fails": c, "diff": d,
+            "diff_ci95": [d - 1.96 * se, d + 1.96 * se]}
+
+
+def fer_entry(err: np.ndarray) -> dict:
+    k, n = int(err.sum()), len(err)
+    return {"frames": n, "errors": k, "fer": k / n, "fer_wilson95": list(wilson(k, n))}
+
+
+def parse_floats(s: str):
+    return [float(x) for x in s.split(",") if x]
+
+
+def emit(line: dict):
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- fer
+
+def study_fer(args):
+    name, mk, Z = MIX[0]
+    code = q.create_code_from(mk(Z))
+    F = 50
+    wk = (code.k + 31) // 32
+    nb = (args.study_frames + F - 1) // F
+    for si, snr in enumerate(parse_floats(args.study_snrs)):
+        decs = {f: q.Decoder(code, F, q.qcldpc_params_init(msg_format=FMT[f])) for f in FMT}
+        acc = {f: {"err": [], "conv": [], "iters": [], "sec": 0.0} for f in FMT}
+        for b in range(nb):
+            llr, syn, key = make_frames(code, F, snr, seed=7_000_000 + 10_000 * si + b)
+            for f, dec in decs.items():
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                dec.decode(llr, syn, args.max_iter)
+                e1.record()
+                e1.synchronize()
+                acc[f]["sec"] += e0.elapsed_time(e1) / 1e3
+                acc[f]["err"].append((dec.keys.view(F, wk) != key).any(1).cpu().numpy())
+                acc[f]["conv"].append(dec.converged.cpu().numpy())
+                acc[f]["iters"].append(dec.iters.cpu().numpy())
+            del llr, syn, key
+        ref = np.concatenate(acc["fp32"]["err"]).astype(np.int64)
+        out = {"study": "fer", "code": f"rate 0.02, Z={Z}, n={code.n}", "snr": snr,
+               "max_iter": args.max_iter, "frames_per_decode": F, "formats": {}}
+        for f in FMT:
+            e = np.concatenate(acc[f]["err"]).astype(np.int64)
+            conv = np.concatenate(acc[f]["conv"])
+            its = np.concatenate(acc[f]["iters"])
+            ent = fer_entry(e)
+            ent.update({"converged": int((conv == 1).sum()),
+                        "undetected": int(((conv == 1) & (e == 1)).sum()),
+                        "mean_iters": float(its.mean()),
+                        "mbps": len(e) * code.n / acc[f]["sec"] / 1e6})
+            if f != "fp32":
+                ent["vs_fp32"] = paired(ref, e)
+            out["formats"][f] = ent
+        emit(out)
+
+
+# ------------------------------------------------------------------- batch
+
+def mix_setup(args, frames_per_code):
+    snrs = parse_floats(args.mix_snrs)
+    codes, inputs = {}, {}
+    for i, (name, mk, Z) in enumerate(MIX):
+        codes[name] = q.create_code_from(mk(Z))
+        inputs[name] = make_frames(codes[name], frames_per_code[name], snrs[i],
+                                   seed=8_000_000 + 1000 * i)
+    return codes, inputs, snrs
+
+
+def split_mix(total: int) -> dict:
+    base, extra = divmod(total, len(MIX))
+    return {name: base + (1 if i < extra else 0) for i, (name, _, _) in enumerate(MIX)}
+
+
+class PoolBatch:
+    """One pool per code with a slot for every frame of the mix. ``run``
+    loads all frames, steps the pools together (one graph launch per step)
+    until every slot stopped, and collects; the slots are free again after."""
+
+    def __init__(self, codes, counts, fmt, max_iter, passes=8):
+        params = q.qcldpc_params_init(msg_format=FMT[fmt])
+        self.codes, self.counts, self.passes = codes, counts, passes
+        self.pools = {c: q.Pool(codes[c], counts[c], max_iter, params) for c in codes}
+        self.ids = {c: torch.arange(counts[c], dtype=torch.int32, device="cuda") for c in codes}
+        self.outs = {c: (torch.empty((counts[c], (codes[c].k + 31) // 32), dtype=torch.int32,
+                                     device="cuda"),
+                         torch.empty(counts[c], dtype=torch.int32, device="cuda"),
+                         torch.empty(counts[c], dtype=torch.int32, device="cuda")) for c in codes}
+
+    def run(self, inputs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in self.codes:
+            llr, syn, _ = inputs[c]
+            q.qcldpc_pool_load(self.pools[c], self.counts[c], self.ids[c], llr, syn)
+        plist = list(self.pools.values())
+        states = torch.cat([p.state for p in plist])
+        while True:
+            q.qcldpc_pools_step(plist, self.passes)
+            torch.cat([p.state for p in plist], out=states)
+            if bool((states == 2).all()):
+                break
+        for c in self.codes:
+            q.qcldpc_pool_collect(self.pools[c], self.counts[c], self.ids[c], *self.outs[c])
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, self.outs
+
+
+class PerFrame:
+    """The plain FP32 decoder, one frame per call: each frame is copied into a
+    fixed staging buffer, so every call reuses the decoder's cached graph
+    (graphs are cached per argument set, buffer addresses included)."""
+
+    def __init__(self, codes):
+        self.codes = codes
+        self.dec = {c: q.Decoder(codes[c], 1, q.qcldpc_params_init()) for c in codes}
+        self.stage = {c: (torch.empty(codes[c].n, device="cuda"),
+                          torch.empty((codes[c].m + 31) // 32, dtype=torch.int32, device="cuda"))
+                      for c in codes}
+
+    def decode(self, c, llr, syn, f, max_iter):
+        n, wm = self.codes[c].n, (self.codes[c].m + 31) // 32
+        self.stage[c][0].copy_(llr[f * n:(f + 1) * n])
+        self.stage[c][1].copy_(syn[f * wm:(f + 1) * wm])
+        d = self.dec[c]
+        d.decode(self.stage[c][0], self.stage[c][1], max_iter)
+        return d
+
+    def run(self, inputs, counts, max_iter):
+        res = {c: (torch.empty((counts[c], (self.codes[c].k + 31) // 32), dtype=torch.int32,
+                               device="cuda"),
+                   torch.empty(counts[c], dtype=torch.int32, device="cuda"),
+                   torch.empty(counts[c], dtype=torch.int32, device="cuda")) for c in self.codes}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in self.codes:
+            llr, syn, _ = inputs[c]
+            for f in range(counts[c]):
+                d = self.decode(c, llr, syn, f, max_iter)
+                res[c][0][f].copy_(d.keys)
+                res[c][1][f:f + 1].copy_(d.converged)
+                res[c][2][f:f + 1].copy_(d.iters)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, res
+
+
+class PerCode:
+    """The plain FP32 decoder, one call per code with all of its frames."""
+
+    def __init__(self, codes, counts):
+        self.codes, self.counts = codes, counts
+        self.dec = {c: q.Decoder(codes[c], counts[c], q.qcldpc_params_init()) for c in codes}
+
+    def run(self, inputs, max_iter):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c in self.codes:
+            llr, syn, _ = inputs[c]
+            self.dec[c].decode(llr, syn, max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res = {}
+        for c in self.codes:
+            d, wk = self.dec[c], (self.codes[c].k + 31) // 32
+            res[c] = (d.keys.view(self.counts[c], wk), d.converged, d.iters)
+        return dt, res
+
+
+def summarise(codes, inputs, counts, sec, res):
+    err_all, bits, info = [], 0, 0
+    per = {}
+    for c in codes:
+        keys, conv, its = res[c]
+        e = (keys != inputs[c][2]).any(1).cpu().numpy().astype(np.int64)
+        err_all.append(e)
+        bits += counts[c] * codes[c].n
+        info += int((e == 0).sum()) * codes[c].k
+        per[c] = {"frames": counts[c], "errors": int(e.sum()),
+                  "converged": int((conv.cpu().numpy() == 1).sum()),
+                  "mean_iters": float(its.float().mean().item()),
+                  "max_iters": int(its.max().item())}
+    e = np.concatenate(err_all)
+    out = fer_entry(e)
+    out.update({"seconds": sec, "mbps": bits / sec / 1e6, "info_mbps": info / sec / 1e6,
+                "frames_per_s": len(e) / sec, "per_code": per})
+    return out, e
+
+
+def study_batch(args):
+    counts = split_mix(args.mix_frames)
+    codes, inputs, snrs = mix_setup(args, counts)
+    pb16 = PoolBatch(codes, counts, "fp16", args.max_iter)
+    pb32 = PoolBatch(codes, counts, "fp32", args.max_iter)
+    per_frame, per_code = PerFrame(codes), PerCode(codes, counts)
+    runs = {
+        "pools_fp16": lambda: pb16.run(inputs),
+        "pools_fp32": lambda: pb32.run(inputs),
+        "per_frame_fp32": lambda: per_frame.run(inputs, counts, args.max_iter),
+        "per_code_fp32": lambda: per_code.run(inputs, args.max_iter),
+    }
+    out = {"study": "batch", "frames": sum(counts.values()), "max_iter": args.max_iter,
+           "mix": {name: {"Z": Z, "n": codes[name].n, "rate": codes[name].k / codes[name].n,
+                          "snr": snrs[i], "frames": counts[name]}
+                   for i, (name, _, Z) in enumerate(MIX)},
+           "runs": {}}
+    errs = {}
+    for key, fn in runs.items():
+        fn()  # warm-up: graphs instantiated, workspaces touched
+        sec, res = fn()
+        out["runs"][key], errs[key] = summarise(codes, inputs, counts, sec, res)
+    for key in runs:
+        if key != "per_frame_fp32":
+            out["runs"][key]["vs_per_frame_fp32"] = paired(errs["per_frame_fp32"], errs[key])
+    out["speedup_pools_fp16_vs_per_frame_fp32"] = (out["runs"]["pools_fp16"]["mbps"]
+                                                   / out["runs"]["per_frame_fp32"]["mbps"])
+    emit(out)
+
+
+# ------------------------------------------------------------------- serve
+
+def serve_once(srv, codes, bank, arrivals, passes):
+    """Real-time run of the continuous-batching server on one arrival trace
+    (the server is idle before and after). arrivals: list of (t_offset_s,
+    code, frame index)."""
+    results = []
+    t0 = time.perf_counter()
+    i, N = 0, len(arrivals)
+    while i < N or srv.pending():
+        now = time.perf_counter() - t0
+        while i < N and arrivals[i][0] <= now:
+            ta, c, f = arrivals[i]
+            llr, syn, _ = bank[c]
+            n, wm = codes[c].n, (codes[c].m + 31) // 32
+            srv.submit(serve.Request(c, llr[f * n:(f + 1) * n], syn[f * wm:(f + 1) * wm],
+                                     tag=(i, c, f), t_arrival=t0 + ta))
+            i += 1
+        if srv.pending():
+            results.extend(srv.tick(passes))
+        elif i < N:
+            time.sleep(max(0.0, arrivals[i][0] - (time.perf_counter() - t0)))
+    t_end = time.perf_counter()
+    lat = np.array([r.latency for r in results])
+    keys_h = {c: bank[c][2].cpu() for c in codes}
+    err = np.array([int((r.keys != keys_h[r.code][r.tag[2]]).any())
+                    for r in sorted(results, key=lambda r: r.tag[0])])
+    return lat, err, t_end - t0
+
+
+def fifo_once(per_frame, bank, max_iter, arrivals):
+    """First-in-first-out server decoding one frame at a time with the plain
+    FP32 decoder."""
+    lat, err = [], []
+    t0 = time.perf_counter()
+    for ta, c, f in arrivals:
+        now = time.perf_counter() - t0
+        if now < ta:
+            time.sleep(ta - now)
+        llr, syn, key = bank[c]
+        d = per_frame.decode(c, llr, syn, f, max_iter)
+        err.append(int((d.keys != key[f]).any().item()))  # waits for the decode
+        lat.append(time.perf_counter() - t0 - ta)
+    return np.array(lat), np.array(err), time.perf_counter() - t0
+
+
+def trace(rng, rate_fps, seconds, n_bank, names, max_requests=3000):
+    N = min(max(20, int(round(rate_fps * seconds))), max_requests)
+    t = np.cumsum(rng.exponential(1.0 / rate_fps, N))
+    cs = rng.integers(0, len(names), N)
+    fs = rng.integers(0, n_bank, N)
+    return [(float(t[j]), names[cs[j]], int(fs[j])) for j in range(N)]
+
+
+def study_serve(args):
+    n_bank = 32
+    counts = {name: n_bank for name, _, _ in MIX}
+    codes, bank, snrs = mix_setup(args, counts)
+    names = [name for name, _, _ in MIX]
+    params = q.qcldpc_params_init(msg_format=FMT["fp16"])
+    slots = {name: 64 for name in names}
+    passes = 4
+    budget = 64 << 30
+    bits = {c: codes[c].n for c in names}
+    # capacity: a saturated burst (every request present at t = 0)
+    rng = np.random.default_rng(12345)
+    burst = [(0.0, names[j % 3], int(rng.integers(0, n_bank))) for j in range(3 * 96)]
+    srv = serve.Server(codes, slots, args.max_iter, params, hbm_budget_bytes=budget)
+    serve_once(srv, codes, bank, burst[:30], passes)  # warm-up: graphs instantiated
+    lat, err, sec = serve_once(srv, codes, bank, burst, passes)
+    footprint = srv.footprint
+    cap_fps = len(burst) / sec
+    per_frame = PerFrame(codes)
+    fifo_once(per_frame, bank, args.max_iter, burst[:12])  # warm-up of the per-frame decoder
+    emit({"study": "serve", "phase": "capacity", "frames": len(burst), "seconds": sec,
+          "frames_per_s": cap_fps,
+          "mbps": sum(bits[c] for _, c, _ in burst) / sec / 1e6,
+          "slots": slots, "passes_per_tick": passes, "msg_format": "fp16",
+          "device_footprint_bytes": footprint,
+          "mix": {name: {"n": codes[name].n, "snr": snrs[i]} for i, name in enumerate(names)}})
+    for li, load in enumerate(parse_floats(args.loads)):
+        arr = trace(np.random.default_rng(1000 + li), load * cap_fps, args.serve_seconds, n_bank,
+                    names)
+        lat, err, sec = serve_once(srv, codes, bank, arr, passes)
+        flat, ferr, fsec = fifo_once(per_frame, bank, args.max_iter, arr)
+        total_bits = sum(bits[c] for _, c, _ in arr)
+        emit({"study": "serve", "load": load, "offered_fps": load * cap_fps, "requests": len(arr),
+              "server": {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                         "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                         "mbps": total_bits / sec / 1e6, **fer_entry(err)},
+              "per_frame_fifo_fp32": {"p50_ms": 1e3 * float(np.percentile(flat, 50)),
+                                      "p99_ms": 1e3 * float(np.percentile(flat, 99)),
+                                      "mbps": total_bits / fsec / 1e6, **fer_entry(ferr)},
+              "vs_fifo": paired(ferr, err)})
+
+
+def run(args):
+    torch.cuda.set_device(0)
+    q.load()
+    {"fer": study_fer, "batch": study_batch, "serve": study_serve}[args.study](args)

@@ -9,8 +9,9 @@ Each ``tick``:
    straight from the request's own device buffers);
 2. steps every pool by ``passes`` iteration passes in one graph launch
    (``qcldpc_pools_step``), so frames of all codes and all ages share the GPU;
-3. reads the slot states and collects stopped frames (``qcldpc_pool_collect``),
-   which frees their slots for the next tick.
+3. reads the slot states of all pools in one device-to-host copy and collects
+   each pool's stopped frames in one ``qcldpc_pool_collect``, which frees
+   their slots for the next tick.
 
 Host-side scheduling only: all decoding runs in libqcldpc.
 """
@@ -88,27 +89,38 @@ class Server:
                 s = self.free[name].popleft()
                 q.qcldpc_pool_load(pool, 1, ids[s:s + 1], req.llr, req.syn, self.stream)
                 self.busy[name][s] = req
-        active = [p for name, p in self.pools.items() if self.busy[name]]
-        if active:
-            q.qcldpc_pools_step(active, passes, self.stream)
-        done = []
-        for name, pool in self.pools.items():
-            if not self.busy[name]:
+        names = [name for name in self.pools if self.busy[name]]
+        if not names:
+            return []
+        q.qcldpc_pools_step([self.pools[name] for name in names], passes, self.stream)
+        # one device->host read of every busy pool's slot states (waits for the passes)
+        with torch.cuda.stream(self.stream):
+            states = torch.cat([self.pools[name].state for name in names]).cpu().tolist()
+        now = time.perf_counter()
+        done, collected, off = [], [], 0
+        for name in names:
+            pool = self.pools[name]
+            st = states[off: off + pool.n_slots]
+            off += pool.n_slots
+            stopped = [s for s in self.busy[name] if st[s] == 2]
+            if not stopped:
                 continue
-            state = pool.state.cpu()  # waits for this tick's passes
-            now = time.perf_counter()
             keys, conv, iters = self.out[name]
-            ids = self.slot_ids[name]
-            stopped = [s for s in self.busy[name] if int(state[s]) == 2]
-            for s in stopped:
-                q.qcldpc_pool_collect(pool, 1, ids[s:s + 1], keys[s], conv[s:s + 1], iters[s:s + 1],
-                                      self.stream)
-            if stopped:
-                k_h, c_h, i_h = keys.cpu(), conv.cpu(), iters.cpu()
-                for s in stopped:
+            with torch.cuda.stream(self.stream):
+                sel = torch.tensor(stopped, dtype=torch.int32).to(self.slot_ids[name].device)
+            n = len(stopped)
+            q.qcldpc_pool_collect(pool, n, sel, keys[:n], conv[:n], iters[:n], self.stream)
+            collected.append((name, stopped))
+        if collected:
+            with torch.cuda.stream(self.stream):
+                host = {name: tuple(t[:len(stopped)].cpu() for t in self.out[name])
+                        for name, stopped in collected}
+            for name, stopped in collected:
+                k_h, c_h, i_h = host[name]
+                for j, s in enumerate(stopped):
                     req = self.busy[name].pop(s)
                     self.free[name].append(s)
-                    done.append(Result(req.tag, name, k_h[s].clone(), int(c_h[s]), int(i_h[s]),
+                    done.append(Result(req.tag, name, k_h[j].clone(), int(c_h[j]), int(i_h[j]),
                                        req.t_arrival, now))
         return done
 
