@@ -91,6 +91,14 @@ constexpr int kGraphCacheSize = 8;
 #define QCLDPC_CN_TVPT 4
 #endif
 constexpr int kTmaVpt = QCLDPC_CN_TVPT;
+// Resident blocks per SM the staged pass is compiled for (caps registers).
+#ifndef QCLDPC_CN_TMA_MINBLOCKS
+#define QCLDPC_CN_TMA_MINBLOCKS 5
+#endif
+// Evaluate a thread's checks two at a time in packed FP32x2 arithmetic.
+#ifndef QCLDPC_CN_PAIR
+#define QCLDPC_CN_PAIR 1
+#endif
 #ifndef QCLDPC_CN_UNROLL
 #define QCLDPC_CN_UNROLL 4
 #endif
@@ -174,6 +182,28 @@ __device__ __forceinline__ float psi_f(float y) {
     const float v = t * t;
     const float a = fmaf(fmaf(fmaf(fmaf(kA4, v, kA3), v, kA2), v, kA1), v, kA0);
     return fmaxf(small, t * a);
+}
+
+// psi_f on two arguments at once with the packed FP32x2 multiply-adds of
+// sm_100-class GPUs. Every packed operation rounds each lane exactly as the
+// scalar fmaf / multiply of psi_f does, so psi2(y).x == psi_f(y.x) bit for
+// bit (kC - lg2 is formed as fma(lg2, -1, kC), the same single rounding).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 psi2(float2 y) {
+    const float2 w = __fmul2_rn(y, y);
+    float2 g = __ffma2_rn(f2(kG3), w, f2(kG2));
+    g = __ffma2_rn(g, w, f2(kG1));
+    g = __ffma2_rn(g, w, f2(kG0));
+    const float2 lc = __ffma2_rn(make_float2(lg2_approx(y.x), lg2_approx(y.y)), f2(-1.0f), f2(kC));
+    const float2 small = __ffma2_rn(w, g, lc);
+    const float2 t = make_float2(ex2_approx(-y.x), ex2_approx(-y.y));
+    const float2 v = __fmul2_rn(t, t);
+    float2 a = __ffma2_rn(f2(kA4), v, f2(kA3));
+    a = __ffma2_rn(a, v, f2(kA2));
+    a = __ffma2_rn(a, v, f2(kA1));
+    a = __ffma2_rn(a, v, f2(kA0));
+    const float2 ta = __fmul2_rn(t, a);
+    return make_float2(fmaxf(small.x, ta.x), fmaxf(small.y, ta.y));
 }
 
 constexpr uint32_t kSign = 0x80000000u;
@@ -571,6 +601,21 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, const Work &W) {
     return false;
 }
 
+// Soft output of a degree-1 neighbour (row entry e, check i) at iteration t:
+// its posterior Q_p + m_cp in natural units, where the message has sign sk
+// and psi-domain magnitude psi(ex) (clipped).
+__device__ __noinline__ void soft_deg1(const Table &T, const Work &W, int f, int t, int e, int i,
+                                       float ex, uint32_t sk) {
+    const int Z = T.Z;
+    const qc::RowEnt re = T.rows[e];
+    int vo = i + re.shift;
+    if (vo >= Z) vo -= Z;
+    const float mag = fminf(psi_f(ex), W.clip);
+    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
+    post1[T.row_off_a[e] + i] =
+        W.llr[(size_t)f * W.n + (size_t)re.col * Z + vo] + kLn2 * __uint_as_float(fbits(mag) ^ sk);
+}
+
 template <int NH, int ND, int MODE, typename M>
 __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int t,
                                         unsigned char *smem) {
@@ -679,14 +724,106 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     const int dsh = 31 - (tid & 31);
     const bool lane0 = (tid & 31) == 0;
 
+    // syndrome words of the owned checks, loaded while the copies are in flight
+    uint32_t sw[kTmaVpt];
+#pragma unroll
+    for (int c = 0; c < kTmaVpt; c++)
+        sw[c] = i0 + c * kThreads + tid < Z ? (__ldg(sy + c * kWordStep) << ssh) : 0u;
+
     const bool staged = stage_wait(bar, W);
     bool bad = false;
     if (staged) {
+      if constexpr (QCLDPC_CN_PAIR && kTmaVpt % 2 == 0) {
+        // Two checks (c, c + 1) per step, their arithmetic in packed FP32x2
+        // operations (per lane identical to the scalar path below).
+#pragma unroll kCnUnroll
+        for (int c = 0; c < kTmaVpt; c += 2) {
+            const int ia = i0 + c * kThreads + tid, ib = ia + kThreads;
+            const bool va = ia < Z, vb = ib < Z;
+            float2 lv[NHa], phi[D];
+            uint32_t sga[D], sgb[D];
+            uint32_t sta = sw[c], stb = sw[c + 1], pa = sw[c], pb = sw[c + 1];
+#pragma unroll
+            for (int k = 0; k < NH; k++) {
+                lv[k] = make_float2(pL[k][c * kThreads], pL[k][(c + 1) * kThreads]);
+                pa ^= fbits(lv[k].x);
+                pb ^= fbits(lv[k].y);
+            }
+            if (kTest) {
+#pragma unroll
+                for (int k = 0; k < ND; k++) {
+                    pa ^= pB[k][c * kWordStep] << dsh;
+                    pb ^= pB[k][(c + 1) * kWordStep] << dsh;
+                }
+                bad |= (va && (pa & kSign) != 0) || (vb && (pb & kSign) != 0);
+            }
+            if constexpr (kUpdate) {
+#pragma unroll
+                for (int k = 0; k < NH; k++) {
+                    float2 d = lv[k];
+                    if (kReadMsg) {
+                        const float2 m = make_float2(Codec<M>::dec(pM[k][c * kThreads], W),
+                                                     Codec<M>::dec(pM[k][(c + 1) * kThreads], W));
+                        d = __ffma2_rn(m, f2(-1.0f), d);  // lv - m, one rounding
+                    }
+                    phi[k] = psi2(make_float2(fminf(fmaxf(fabsf(d.x), W.xmin), W.clip),
+                                              fminf(fmaxf(fabsf(d.y), W.xmin), W.clip)));
+                    sga[k] = fbits(d.x);
+                    sgb[k] = fbits(d.y);
+                    sta ^= sga[k];
+                    stb ^= sgb[k];
+                }
+#pragma unroll
+                for (int k = 0; k < ND; k++) {
+                    const float qa = pP[k][c * kThreads], qb = pP[k][(c + 1) * kThreads];
+                    phi[NH + k] = make_float2(fabsf(qa), fabsf(qb));
+                    sga[NH + k] = fbits(qa);
+                    sgb[NH + k] = fbits(qb);
+                    sta ^= sga[NH + k];
+                    stb ^= sgb[NH + k];
+                }
+                // exclusive sums by prefix / suffix (psi >= +0, so 0 + x = x)
+                float2 pre[D], suf[D];
+                pre[0] = phi[0];
+#pragma unroll
+                for (int k = 1; k < D; k++) pre[k] = __fadd2_rn(pre[k - 1], phi[k]);
+                suf[D - 1] = phi[D - 1];
+#pragma unroll
+                for (int k = D - 2; k >= 0; k--) suf[k] = __fadd2_rn(suf[k + 1], phi[k]);
+#pragma unroll
+                for (int k = 0; k < D; k++) {
+                    const float2 s2 = k == 0       ? suf[1]
+                                      : k == D - 1 ? pre[D - 2]
+                                                   : __fadd2_rn(pre[k - 1], suf[k + 1]);
+                    const float2 ex = make_float2(fmaxf(s2.x, W.xmin), fmaxf(s2.y, W.xmin));
+                    const uint32_t ska = (sta ^ sga[k]) & kSign, skb = (stb ^ sgb[k]) & kSign;
+                    if (k < NH) {
+                        const float2 mag = psi2(ex);
+                        if (va) oM[k][c * kThreads] =
+                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.x, W.clip)) ^ ska), W);
+                        if (vb) oM[k][(c + 1) * kThreads] =
+                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.y, W.clip)) ^ skb), W);
+                    } else {
+                        const uint32_t da = ex.x < phi[k].x ? ska : (sga[k] & kSign);
+                        const uint32_t db = ex.y < phi[k].y ? skb : (sgb[k] & kSign);
+                        const uint32_t wa = __ballot_sync(0xffffffffu, va && da != 0);
+                        const uint32_t wb = __ballot_sync(0xffffffffu, vb && db != 0);
+                        if (lane0 && va) oB[k - NH][c * kWordStep] = wa;
+                        if (lane0 && vb) oB[k - NH][(c + 1) * kWordStep] = wb;
+                        if (W.soft) {
+                            if (va) soft_deg1(T, W, f, t, rp + k, ia, ex.x, ska);
+                            if (vb) soft_deg1(T, W, f, t, rp + k, ib, ex.y, skb);
+                        }
+                    }
+                }
+            }
+        }
+      } else {
 #pragma unroll kCnUnroll
         for (int c = 0; c < kTmaVpt; c++) {
             const int i = i0 + c * kThreads + tid;
             const bool valid = i < Z;
-            const uint32_t sb = valid ? (__ldg(sy + c * kWordStep) << ssh) : 0u;
+            const uint32_t sb = sw[c];
             float lv[NHa], phi[D];
             uint32_t sg[D];
             uint32_t stot = sb, par = sb;
@@ -733,20 +870,12 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
                         const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
                         const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
                         if (lane0 && valid) oB[k - NH][c * kWordStep] = word;
-                        if (W.soft && valid) {
-                            const qc::RowEnt e = T.rows[rp + k];
-                            int vo = i + e.shift;
-                            if (vo >= Z) vo -= Z;
-                            const float mag = fminf(psi_f(ex), W.clip);
-                            float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
-                            post1[T.row_off_a[rp + k] + i] =
-                                W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
-                                kLn2 * __uint_as_float(fbits(mag) ^ sk);
-                        }
+                        if (W.soft && valid) soft_deg1(T, W, f, t, rp + k, i, ex, sk);
                     }
                 }
             }
         }
+      }
     }
     __syncthreads();
     if (tid == 0) mbar_inval(bar);
@@ -824,7 +953,7 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const
 // row, frame), dynamic shared memory sized by cn_tma_smem for the code's
 // widest exact-shape row. Rows of other shapes take the register path.
 template <int MAXD, typename M>
-__global__ void __launch_bounds__(kThreads) cn_tma_kernel(const __grid_constant__ Table T,
+__global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kernel(const __grid_constant__ Table T,
                                                           const __grid_constant__ Work W) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int f = blockIdx.z;
