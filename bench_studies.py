@@ -4,10 +4,10 @@
   in FP32, FP16 and int8 (arithmetic FP32); per format the frame error rate
   with its Wilson 95 % interval, the paired difference to FP32 with its 95 %
   interval, mean iterations and decoded Mbit/s.
-* ``batch``: 256 frames mixing three rates (0.02 at n = 10^6, 0.05 at
-  n = 5*10^5, 0.10 at n = 10^5) decoded together by frame pools stepped in one
-  graph launch (FP16 and FP32 messages), against the plain FP32 decoder run
-  one frame at a time and one code at a time.
+* ``batch``: 256 frames drawn uniformly from nine codes (rates 0.02, 0.05
+  and 0.10, each at n = 10^5, 4*10^5 and 10^6) decoded together by frame
+  pools stepped in one graph launch (FP16 and FP32 messages), against the
+  plain FP32 decoder run one frame at a time and one code at a time.
 * ``serve``: Poisson arrivals of frames of the same mix into the
   continuous-batching server (FP16 messages) at offered loads from 10 % to
   120 % of its measured capacity; p50/p99 frame latency and served Mbit/s,
@@ -35,9 +35,11 @@ from bench import wilson
 from paper_1702_07740_gb300 import qcldpc as q
 from paper_1702_07740_gb300 import serve
 
-MIX = (("r002", synth.rate002_code, 20000),
-       ("r005", synth.rate005_code, 25000),
-       ("r010", synth.rate010_code, 10000))
+# The mixed-rate workload: three rates, each at n = 10^5, 4*10^5 and 10^6.
+RATES = (("r002", synth.rate002_code, (2000, 8000, 20000)),
+         ("r005", synth.rate005_code, (5000, 20000, 50000)),
+         ("r010", synth.rate010_code, (10000, 40000, 100000)))
+MIX = tuple((f"{name}_z{Z}", mk, Z, ri) for ri, (name, mk, Zs) in enumerate(RATES) for Z in Zs)
 FMT = {"fp32": 0, "fp16": 1, "int8": 2}
 
 
@@ -102,8 +104,8 @@ def emit(line: dict):
 # --------------------------------------------------------------------- fer
 
 def study_fer(args):
-    name, mk, Z = MIX[0]
-    code = q.create_code_from(mk(Z))
+    Z = 20000
+    code = q.create_code_from(synth.rate002_code(Z))
     F = 50
     wk = (code.k + 31) // 32
     nb = (args.study_frames + F - 1) // F
@@ -144,18 +146,23 @@ def study_fer(args):
 # ------------------------------------------------------------------- batch
 
 def mix_setup(args, frames_per_code):
-    snrs = parse_floats(args.mix_snrs)
-    codes, inputs = {}, {}
-    for i, (name, mk, Z) in enumerate(MIX):
+    """Codes of the mix and their frames; the SNR is set per rate."""
+    snr_of_rate = parse_floats(args.mix_snrs)
+    codes, inputs, snrs = {}, {}, {}
+    for i, (name, mk, Z, ri) in enumerate(MIX):
+        if frames_per_code.get(name, 0) == 0:
+            continue
         codes[name] = q.create_code_from(mk(Z))
-        inputs[name] = make_frames(codes[name], frames_per_code[name], snrs[i],
+        snrs[name] = snr_of_rate[ri]
+        inputs[name] = make_frames(codes[name], frames_per_code[name], snrs[name],
                                    seed=8_000_000 + 1000 * i)
     return codes, inputs, snrs
 
 
-def split_mix(total: int) -> dict:
-    base, extra = divmod(total, len(MIX))
-    return {name: base + (1 if i < extra else 0) for i, (name, _, _) in enumerate(MIX)}
+def split_mix(total: int, seed: int = 4) -> dict:
+    """Frames per code of a seeded uniform draw over the codes of the mix."""
+    draw = np.random.default_rng(seed).integers(0, len(MIX), total)
+    return {name: int((draw == i).sum()) for i, (name, _, _, _) in enumerate(MIX)}
 
 
 class PoolBatch:
@@ -273,7 +280,7 @@ def summarise(codes, inputs, counts, sec, res):
 
 
 def study_batch(args):
-    counts = split_mix(args.mix_frames)
+    counts = {c: k for c, k in split_mix(args.mix_frames).items() if k > 0}
     codes, inputs, snrs = mix_setup(args, counts)
     pb16 = PoolBatch(codes, counts, "fp16", args.max_iter)
     pb32 = PoolBatch(codes, counts, "fp32", args.max_iter)
@@ -286,8 +293,8 @@ def study_batch(args):
     }
     out = {"study": "batch", "frames": sum(counts.values()), "max_iter": args.max_iter,
            "mix": {name: {"Z": Z, "n": codes[name].n, "rate": codes[name].k / codes[name].n,
-                          "snr": snrs[i], "frames": counts[name]}
-                   for i, (name, _, Z) in enumerate(MIX)},
+                          "snr": snrs[name], "frames": counts[name]}
+                   for name, _, Z, _ in MIX if name in codes},
            "runs": {}}
     errs = {}
     for key, fn in runs.items():
@@ -348,8 +355,8 @@ def fifo_once(per_frame, bank, max_iter, arrivals):
     return np.array(lat), np.array(err), time.perf_counter() - t0
 
 
-def trace(rng, rate_fps, seconds, n_bank, names, max_requests=3000):
-    N = min(max(20, int(round(rate_fps * seconds))), max_requests)
+def trace(rng, rate_fps, N, n_bank, names):
+    """N Poisson arrivals at rate_fps, each a uniformly drawn code and frame."""
     t = np.cumsum(rng.exponential(1.0 / rate_fps, N))
     cs = rng.integers(0, len(names), N)
     fs = rng.integers(0, n_bank, N)
@@ -357,18 +364,19 @@ def trace(rng, rate_fps, seconds, n_bank, names, max_requests=3000):
 
 
 def study_serve(args):
-    n_bank = 32
-    counts = {name: n_bank for name, _, _ in MIX}
+    n_bank = 16
+    counts = {name: n_bank for name, _, _, _ in MIX}
     codes, bank, snrs = mix_setup(args, counts)
-    names = [name for name, _, _ in MIX]
+    names = [name for name, _, _, _ in MIX]
     params = q.qcldpc_params_init(msg_format=FMT["fp16"])
-    slots = {name: 64 for name in names}
+    slots = {name: 32 for name in names}
     passes = 4
     budget = 64 << 30
     bits = {c: codes[c].n for c in names}
     # capacity: a saturated burst (every request present at t = 0)
     rng = np.random.default_rng(12345)
-    burst = [(0.0, names[j % 3], int(rng.integers(0, n_bank))) for j in range(3 * 96)]
+    burst = [(0.0, names[j % len(names)], int(rng.integers(0, n_bank)))
+             for j in range(len(names) * 64)]
     srv = serve.Server(codes, slots, args.max_iter, params, hbm_budget_bytes=budget)
     serve_once(srv, codes, bank, burst[:30], passes)  # warm-up: graphs instantiated
     lat, err, sec = serve_once(srv, codes, bank, burst, passes)
@@ -381,9 +389,9 @@ def study_serve(args):
           "mbps": sum(bits[c] for _, c, _ in burst) / sec / 1e6,
           "slots": slots, "passes_per_tick": passes, "msg_format": "fp16",
           "device_footprint_bytes": footprint,
-          "mix": {name: {"n": codes[name].n, "snr": snrs[i]} for i, name in enumerate(names)}})
+          "mix": {name: {"n": codes[name].n, "snr": snrs[name]} for name in names}})
     for li, load in enumerate(parse_floats(args.loads)):
-        arr = trace(np.random.default_rng(1000 + li), load * cap_fps, args.serve_seconds, n_bank,
+        arr = trace(np.random.default_rng(1000 + li), load * cap_fps, args.serve_requests, n_bank,
                     names)
         lat, err, sec = serve_once(srv, codes, bank, arr, passes)
         flat, ferr, fsec = fifo_once(per_frame, bank, args.max_iter, arr)
