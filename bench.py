@@ -65,14 +65,15 @@ def parse_args():
                     help="instead of the throughput line: FER per message format (fer), a "
                          "mixed-rate 256-frame batch (batch) or a serving-load sweep (serve)")
     ap.add_argument("--study-frames", type=int, default=2000, help="fer: frames per SNR")
-    ap.add_argument("--study-snrs", default="0.13,0.16", help="fer: SNRs of the rate-0.02 code")
+    ap.add_argument("--fer-points", default="r002:0.13,r002:0.16,r005:0.5,r010:1.0",
+                    help="fer: code:SNR operating points (codes r002, r005, r010 at n = 1e6)")
     ap.add_argument("--mix-snrs", default="0.16,0.5,1.0",
-                    help="batch/serve: SNR of the rate 0.02 / 0.05 / 0.10 codes")
+                    help="batch/serve: SNR of the rate 0.02 / 0.05 / 0.10 codes (every length)")
     ap.add_argument("--mix-frames", type=int, default=256, help="batch: frames in the mix")
-    ap.add_argument("--loads", default="0.1,0.25,0.5,0.75,0.9,1.0,1.2",
+    ap.add_argument("--loads", default="0.1,0.2,0.3,0.4,0.5,0.6,0.7,0.8,0.9,1.0,1.1,1.2",
                     help="serve: offered load as a fraction of the measured batched capacity")
-    ap.add_argument("--serve-seconds", type=float, default=3.0,
-                    help="serve: arrival window per load point")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="serve: Poisson arrivals per load point")
     return ap.parse_args()
 
 
@@ -379,7 +380,8 @@ def run_ours(args, world, rank, local):
         loop_passes.append(int(its.max()) + 1)
     frames_total = B * F
     fer = frame_err / frames_total
-    launches = sum(1 + 3 + 3 * loop_passes[s % B] for s in range(args.steps))
+    # per step: llr + init + final, and check pass + control + variable pass per loop pass
+    launches = sum(3 + 3 * loop_passes[s % B] for s in range(args.steps))
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host
     stage = {"x": torch.empty(F * n, dtype=torch.float32, device=dev),

@@ -1,7 +1,8 @@
 """Studies beside bench.py's throughput line (``bench.py --study ...``).
 
-* ``fer``: the same seeded n = 10^6 frames decoded with edge messages stored
-  in FP32, FP16 and int8 (arithmetic FP32); per format the frame error rate
+* ``fer``: the same seeded n = 10^6 frames (rates 0.02, 0.05, 0.10) decoded
+  with edge messages stored in FP32, FP16 and int8 (arithmetic FP32); per
+  format and operating point the frame error rate
   with its Wilson 95 % interval, the paired difference to FP32 with its 95 %
   interval, mean iterations and decoded Mbit/s.
 * ``batch``: 256 frames drawn uniformly from nine codes (rates 0.02, 0.05
@@ -103,13 +104,21 @@ def emit(line: dict):
 
 # --------------------------------------------------------------------- fer
 
+# n = 10^6 member of each rate, for the FER study
+FER_CODES = {"r002": (synth.rate002_code, 20000, "rate 0.02"),
+             "r005": (synth.rate005_code, 50000, "rate 0.05"),
+             "r010": (synth.rate010_code, 100000, "rate 0.10")}
+
+
 def study_fer(args):
-    Z = 20000
-    code = q.create_code_from(synth.rate002_code(Z))
     F = 50
-    wk = (code.k + 31) // 32
     nb = (args.study_frames + F - 1) // F
-    for si, snr in enumerate(parse_floats(args.study_snrs)):
+    for si, item in enumerate(args.fer_points.split(",")):
+        cname, snr = item.split(":")
+        snr = float(snr)
+        mk, Z, label = FER_CODES[cname]
+        code = q.create_code_from(mk(Z))
+        wk = (code.k + 31) // 32
         decs = {f: q.Decoder(code, F, q.qcldpc_params_init(msg_format=FMT[f])) for f in FMT}
         acc = {f: {"err": [], "conv": [], "iters": [], "sec": 0.0} for f in FMT}
         for b in range(nb):
@@ -126,7 +135,7 @@ def study_fer(args):
                 acc[f]["iters"].append(dec.iters.cpu().numpy())
             del llr, syn, key
         ref = np.concatenate(acc["fp32"]["err"]).astype(np.int64)
-        out = {"study": "fer", "code": f"rate 0.02, Z={Z}, n={code.n}", "snr": snr,
+        out = {"study": "fer", "code": f"{label}, Z={Z}, n={code.n}", "snr": snr,
                "max_iter": args.max_iter, "frames_per_decode": F, "formats": {}}
         for f in FMT:
             e = np.concatenate(acc[f]["err"]).astype(np.int64)
@@ -364,7 +373,7 @@ def trace(rng, rate_fps, N, n_bank, names):
 
 
 def study_serve(args):
-    n_bank = 16
+    n_bank = 64
     counts = {name: n_bank for name, _, _, _ in MIX}
     codes, bank, snrs = mix_setup(args, counts)
     names = [name for name, _, _, _ in MIX]

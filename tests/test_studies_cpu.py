@@ -32,8 +32,11 @@ def test_paired_difference_counts_discordant_frames():
 
 def test_split_mix_and_trace():
     counts = bench_studies.split_mix(256)
-    assert sum(counts.values()) == 256 and max(counts.values()) - min(counts.values()) <= 1
-    tr = bench_studies.trace(np.random.default_rng(0), 100.0, 2.0, 32, ["a", "b", "c"])
+    assert sum(counts.values()) == 256 and len(counts) == 9
+    assert min(counts.values()) >= 10  # every code of the mix is present
+    ns = {mk(Z)["nb"] * Z for _, mk, Z, _ in bench_studies.MIX}
+    assert ns == {100000, 400000, 1000000}
+    tr = bench_studies.trace(np.random.default_rng(0), 100.0, 200, 32, ["a", "b", "c"])
     t = np.array([x[0] for x in tr])
     assert len(tr) == 200 and np.all(np.diff(t) > 0)
     assert {x[1] for x in tr} == {"a", "b", "c"}
