@@ -20,7 +20,7 @@
 // itself (Step 4 of Algorithm 1 for degree-1 nodes).
 //
 // One iteration t is two streaming kernels plus a one-block control kernel:
-//   cn_kernel   per check c (row r, offset i): L_vc = clip(L_v - m_cv(t-1)) for
+//   cn_tma_kernel per check c (row r, offset i): L_vc = clip(L_v - m_cv(t-1)) for
 //               heavy neighbours v = (col, (i+s) mod Z), Phi-domain exclusive
 //               sums, m_cv(t) written back in place; decisions of the degree-1
 //               neighbours of iteration t. It also evaluates the stop test of
@@ -31,7 +31,7 @@
 //               graph's loop condition.
 //   vn_kernel   per heavy variable v: L_v = Q_v + sum over its ~60 circulants
 //               of m_cv, read at offsets (j - s) mod Z (coalesced, one wrap).
-// A last pass (t = max_iter + 1) runs cn_kernel as a pure stop test.
+// A last pass (t = max_iter + 1) runs cn_tma_kernel as a pure stop test.
 //
 // All call arguments travel as one __grid_constant__ parameter (Work), so
 // they sit in the constant bank as warp-uniform operands; instantiated graphs
@@ -64,12 +64,6 @@ using qc::Table;
 
 // Launch shapes (overridable at build time for tuning sweeps). Defaults
 // from a sweep at Z = 20,000 with 16 frames on GB300.
-#ifndef QCLDPC_CN_VPT
-#define QCLDPC_CN_VPT 4
-#endif
-#ifndef QCLDPC_CN_MINBLOCKS
-#define QCLDPC_CN_MINBLOCKS 3
-#endif
 #ifndef QCLDPC_VN_VPT
 #define QCLDPC_VN_VPT 2
 #endif
@@ -77,16 +71,12 @@ using qc::Table;
 #define QCLDPC_VN_UNROLL 6
 #endif
 constexpr int kThreads = 256;
-constexpr int kCnVpt = QCLDPC_CN_VPT;  // checks per thread (interleaved by kThreads)
 constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
 constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
 constexpr int kCtrlThreads = 256;
 constexpr int kGraphCacheSize = 8;
 // Check-node pass with bulk-copy staging: one block stages kTile consecutive
 // checks of one base row (kTmaVpt per thread) into shared memory.
-#ifndef QCLDPC_CN_TMA
-#define QCLDPC_CN_TMA 1
-#endif
 #ifndef QCLDPC_CN_TVPT
 #define QCLDPC_CN_TVPT 4
 #endif
@@ -294,153 +284,6 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
 // messages; later iterations read them; the stop test of iteration t-1 runs
 // when t-1 >= et_start; the pass after the last iteration only tests.
 enum CnMode { kFirst = 0, kSteady = 1, kSteadyTest = 2, kTestOnly = 3 };
-
-// Rows with exactly NH heavy and ND degree-1 circulants, pass mode MODE.
-//
-// Phase 1 issues every load of the kCnVpt owned checks (offsets i0 + u *
-// kThreads) before any Phi evaluation, so a thread keeps all its edges in
-// flight at once. Lanes past the end of the row load from the padding and
-// never store.
-//
-// Phase 2, per check: the stop test of iteration t-1 (syndrome bit, heavy
-// posterior signs, degree-1 decisions of t-1); then L_vc = clip(L_v - m_cv),
-// Phi of every input, exclusive Phi sums by prefix/suffix (no subtraction,
-// so no cancellation), and signs as XOR of IEEE sign bits:
-//   sign(m_cv) = s_c xor (xor over all inputs) xor (own input).
-// Degree-1 neighbour p: C_p = [Q_p + m_cp < 0]; Phi is decreasing, so
-// |m_cp| > |Q_p| iff the exclusive sum is below Phi(|Q_p|).
-// Returns true if a check of iteration t-1 failed.
-template <int NH, int ND, int MODE>
-__device__ __forceinline__ bool cn_row(const Table &T, const Work &W, int f, int r, int t) {
-    constexpr int D = NH + ND;
-    constexpr int NHa = NH > 0 ? NH : 1;
-    constexpr int NDa = ND > 0 ? ND : 1;
-    constexpr bool kUpdate = MODE != kTestOnly;
-    constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
-    constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
-    constexpr int kWordStep = kThreads / 32;  // decision/syndrome words between owned checks
-    const int Z = T.Z, ZW = W.ZW;
-    const int rp = T.row_ptr[r];
-    const int lane = threadIdx.x & 31;
-    const int i0 = blockIdx.x * (kThreads * kCnVpt) + threadIdx.x;
-    const size_t bstride = (size_t)T.n_d1 * ZW;
-
-    // Per-edge pointers at this thread's first check; the other owned checks
-    // sit at fixed offsets (u * kThreads elements, u * kWordStep words).
-    const float *Lp[NHa];
-    float *Mp[NHa];
-    const float *Pp[NDa];
-    const uint32_t *Bp[NDa];
-    uint32_t *Bc[NDa];
-    {
-        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z + i0;
-        float *msg = static_cast<float *>(W.msg) + (size_t)f * T.n_h * Z + i0;
-        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z + i0;
-        const uint32_t *bprev =
-            W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride + (i0 >> 5);
-        uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride + (i0 >> 5);
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
-            if (k < NH) {
-                Lp[k] = L + oa;
-                Mp[k] = msg + ob;
-            } else {
-                Pp[k - NH] = phiq + oa;
-                Bp[k - NH] = bprev + ob;
-                Bc[k - NH] = bcur + ob;
-            }
-        }
-    }
-    const int c0 = r * Z + i0;  // check index of the first owned check
-    const uint32_t *Sp = W.syn + (size_t)f * W.words_m + (c0 >> 5);
-    const int ssh = 31 - (c0 & 31);  // moves s_c to bit 31
-    const int dsh = 31 - lane;       // moves a degree-1 decision bit to bit 31
-
-    // ---- phase 1: every load (lanes past the row read padding; the
-    // syndrome, a caller buffer, is read only for valid checks)
-    float lv[kCnVpt][NHa], mo[kCnVpt][NHa], pq[kCnVpt][NDa];
-    uint32_t sb[kCnVpt], par[kCnVpt];
-#pragma unroll
-    for (int u = 0; u < kCnVpt; u++) {
-        const bool valid = i0 + u * kThreads < Z;
-        sb[u] = valid ? (__ldg(Sp + u * kWordStep) << ssh) : 0u;
-        par[u] = 0;
-#pragma unroll
-        for (int k = 0; k < NH; k++) {
-            lv[u][k] = Lp[k][u * kThreads];
-            mo[u][k] = kReadMsg ? Mp[k][u * kThreads] : 0.0f;
-        }
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-            pq[u][k] = kUpdate ? __ldg(Pp[k] + u * kThreads) : 0.0f;
-            if (kTest) par[u] ^= __ldg(Bp[k] + u * kWordStep) << dsh;
-        }
-    }
-
-    // ---- phase 2
-    bool bad = false;
-#pragma unroll
-    for (int u = 0; u < kCnVpt; u++) {
-        const int i = i0 + u * kThreads;
-        const bool valid = i < Z;
-        if (kTest) {
-            uint32_t p = sb[u] ^ par[u];
-#pragma unroll
-            for (int k = 0; k < NH; k++) p ^= fbits(lv[u][k]);
-            bad |= valid && (p & kSign) != 0;
-        }
-        if constexpr (kUpdate) {
-        float phi[D];
-        uint32_t sg[D];
-        uint32_t stot = sb[u];
-#pragma unroll
-        for (int k = 0; k < NH; k++) {
-            const float d = lv[u][k] - mo[u][k];
-            phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
-            sg[k] = fbits(d);
-            stot ^= sg[k];
-        }
-#pragma unroll
-        for (int k = 0; k < ND; k++) {
-            phi[NH + k] = fabsf(pq[u][k]);
-            sg[NH + k] = fbits(pq[u][k]);
-            stot ^= sg[NH + k];
-        }
-        float pre[D + 1], suf[D + 1];
-        pre[0] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < D; k++) pre[k + 1] = pre[k] + phi[k];
-        suf[D] = 0.0f;
-#pragma unroll
-        for (int k = D - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
-            const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
-            if (k < NH) {
-                const float mag = fminf(psi_f(ex), W.clip);
-                if (valid) Mp[k][u * kThreads] = __uint_as_float(fbits(mag) ^ sk);
-            } else {
-                const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
-                const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
-                if (lane == 0 && valid) Bc[k - NH][u * kWordStep] = word;
-                if (W.soft && valid) {
-                    const qc::RowEnt e = T.rows[rp + k];
-                    int vo = i + e.shift;
-                    if (vo >= Z) vo -= Z;
-                    const float mag = fminf(psi_f(ex), W.clip);
-                    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
-                    post1[T.row_off_a[rp + k] + i] =
-                        W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
-                        kLn2 * __uint_as_float(fbits(mag) ^ sk);
-                }
-            }
-        }
-        }
-    }
-    return bad;
-}
 
 // Any row shape up to MAXD circulants (heavy first), runtime degree with
 // predication; used for shapes the exact instantiations do not cover.
@@ -897,61 +740,13 @@ __device__ __forceinline__ bool cn_tile_dispatch(const Table &T, const Work &W, 
     }
 }
 
-template <int MODE>
-__device__ __forceinline__ bool cn_dispatch(const Table &T, const Work &W, int f, int r, int t,
-                                            int nh, int nd) {
-    switch (nh * 4 + nd) {
-        case 1 * 4 + 1: return cn_row<1, 1, MODE>(T, W, f, r, t);
-        case 2 * 4 + 0: return cn_row<2, 0, MODE>(T, W, f, r, t);
-        case 2 * 4 + 1: return cn_row<2, 1, MODE>(T, W, f, r, t);
-        case 3 * 4 + 0: return cn_row<3, 0, MODE>(T, W, f, r, t);
-        case 3 * 4 + 1: return cn_row<3, 1, MODE>(T, W, f, r, t);
-        case 4 * 4 + 0: return cn_row<4, 0, MODE>(T, W, f, r, t);
-        case 4 * 4 + 1: return cn_row<4, 1, MODE>(T, W, f, r, t);
-        default: return false;  // not reached: the caller routes other shapes to the fallback
-    }
-}
-
 __host__ __device__ constexpr bool exact_shape(int nh, int nd) {
     return (nd == 1 && nh >= 1 && nh <= 4) || (nd == 0 && nh >= 2 && nh <= 4);
 }
 
-// Check-node pass of iteration t (see the file comment). Grid (tile, base
-// row, frame); one block covers kThreads * kCnVpt consecutive checks of one
-// row of one frame. The row shape and pass mode select an exactly unrolled
-// body (block-uniform switch); MAXD bounds the fallback for other shapes.
-template <int MAXD>
-__global__ void __launch_bounds__(kThreads, QCLDPC_CN_MINBLOCKS) cn_kernel(const __grid_constant__ Table T,
-                                                         const __grid_constant__ Work W) {
-    const int f = blockIdx.z;
-    if (W.active[f] == 0) return;  // block-uniform
-    const int r = T.row_order[blockIdx.y];
-    const int t = W.t[f];
-    const int mode = t > W.max_iter ? kTestOnly
-                     : t == 1       ? kFirst
-                     : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
-    const int nh = T.row_nh[r];
-    const int nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
-    bool bad;
-    if (exact_shape(nh, nd)) {
-        switch (mode) {
-            case kFirst: bad = cn_dispatch<kFirst>(T, W, f, r, t, nh, nd); break;
-            case kSteady: bad = cn_dispatch<kSteady>(T, W, f, r, t, nh, nd); break;
-            case kSteadyTest: bad = cn_dispatch<kSteadyTest>(T, W, f, r, t, nh, nd); break;
-            default: bad = cn_dispatch<kTestOnly>(T, W, f, r, t, nh, nd); break;
-        }
-    } else {
-        bad = cn_row_generic<MAXD, float>(T, W, f, r, t, mode,
-                                          blockIdx.x * (kThreads * kCnVpt) + threadIdx.x, kCnVpt);
-    }
-    if (mode == kSteadyTest || mode == kTestOnly) {
-        if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;
-    }
-}
-
 // Check-node pass of iteration t, staged variant: grid (ceil(Z / kTile), base
 // row, frame), dynamic shared memory sized by cn_tma_smem for the code's
-// widest exact-shape row. Rows of other shapes take the register path.
+// widest exact-shape row. Rows of other shapes take the generic path.
 template <int MAXD, typename M>
 __global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kernel(const __grid_constant__ Table T,
                                                           const __grid_constant__ Work W) {
@@ -1166,11 +961,6 @@ Layout layout_of(const Table &T, int F, bool soft, int fmt) {
     return o;
 }
 
-dim3 cn_grid(const Table &T, int F) {
-    const int span = kThreads * kCnVpt;
-    return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)T.mb, (unsigned)F);
-}
-
 dim3 vn_grid(const Table &T, int F) {
     const int span = kThreads * kVnVpt;
     return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)std::max(T.n_hcols, 1), (unsigned)F);
@@ -1181,12 +971,6 @@ int sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 1;
-}
-
-void *cn_kernel_for(int maxdeg) {
-    if (maxdeg <= 5) return (void *)cn_kernel<5>;
-    if (maxdeg <= 8) return (void *)cn_kernel<8>;
-    return (void *)cn_kernel<16>;
 }
 
 template <typename M>
@@ -1225,7 +1009,7 @@ struct CnLaunch {
 
 CnLaunch cn_launch(const Table &T, int F, int fmt) {
     CnLaunch c;
-    if (QCLDPC_CN_TMA || fmt != 0) {
+    {
         size_t smem = kSmemHeader;
         for (int r = 0; r < T.mb; r++) {
             const int nh = T.row_nh[r], nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
@@ -1244,10 +1028,6 @@ CnLaunch cn_launch(const Table &T, int F, int fmt) {
             raise_smem_cap<__half>(cap);
             raise_smem_cap<int8_t>(cap);
         });
-    } else {
-        c.func = cn_kernel_for(T.max_row_deg);
-        c.grid = cn_grid(T, F);
-        c.smem = 0;
     }
     return c;
 }
