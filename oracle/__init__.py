@@ -68,6 +68,9 @@ def _load():
         lib.orc_decode.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, i32,
                                    dbl, dbl, vp, vp, vp, vp]
         lib.orc_decode.restype = i32
+        lib.orc_decode_layered.argtypes = [i64, i64, i64, vp, vp, vp, vp, i32, vp, i32,
+                                           i32, dbl, dbl, vp, vp, vp, vp]
+        lib.orc_decode_layered.restype = i32
         _lib = lib
         return lib
 
@@ -184,4 +187,38 @@ def decode(code: Code, q: np.ndarray, syn: np.ndarray, max_iter: int,
                             _ptr(conv))
     if rc != 0:
         raise MemoryError("oracle decode: allocation failed")
+    return post, chat, int(iters[0]), bool(conv[0])
+
+
+def row_layers(code: Code, n_groups: int) -> np.ndarray:
+    """Layer of every check when the base rows are split into n_groups
+    contiguous groups in natural order: base row r (checks r*Z .. r*Z+Z-1)
+    belongs to group floor(r * n_groups / mb)."""
+    rows = np.arange(code.m, dtype=np.int64) // code.Z
+    return (rows * n_groups // code.mb).astype(np.int32)
+
+
+def decode_layered(code: Code, q: np.ndarray, syn: np.ndarray, max_iter: int,
+                   layer: np.ndarray, et_start: int = 1, clip: float = CLIP,
+                   xmin: float = XMIN):
+    """Layered sum-product decoding of one frame (an extension of Algorithm
+    1: checks split into layers visited in order, see orc_decode_layered).
+    ``layer[c]`` is the layer of check c. Returns ``(post, chat, iters,
+    converged)`` like ``decode``."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    syn = np.ascontiguousarray(syn, dtype=np.uint8)
+    layer = np.ascontiguousarray(layer, dtype=np.int32)
+    assert q.shape == (code.n,) and syn.shape == (code.m,) and layer.shape == (code.m,)
+    n_layers = int(layer.max()) + 1 if code.m else 1
+    post = np.zeros(code.n, dtype=np.float64)
+    chat = np.zeros(code.n, dtype=np.uint8)
+    iters = np.zeros(1, dtype=np.int32)
+    conv = np.zeros(1, dtype=np.int32)
+    rc = _load().orc_decode_layered(code.n, code.m, code.n_edges, _ptr(code.edge_cn),
+                                    _ptr(code.edge_vn), _ptr(q), _ptr(syn), n_layers,
+                                    _ptr(layer), int(max_iter), int(et_start), float(clip),
+                                    float(xmin), _ptr(post), _ptr(chat), _ptr(iters),
+                                    _ptr(conv))
+    if rc != 0:
+        raise ValueError("oracle layered decode: bad layer ids or allocation failure")
     return post, chat, int(iters[0]), bool(conv[0])

@@ -34,7 +34,12 @@
  *   - sgn(0) = +1; messages in both directions are clipped to [-clip, clip]
  *     (clip <= 0 disables clipping); every Phi argument is floored at xmin;
  *   - the stop test runs after iteration t when t >= et_start, and always
- *     after the last iteration.
+ *     after the last iteration;
+ *   - layered schedule (not in the paper, which uses flooding): checks are
+ *     split into layers visited in order within an iteration; the messages
+ *     of one layer are computed together from the state at the layer's
+ *     start, so a variable with several edges in one layer sees none of the
+ *     layer's own new messages.
  *
  * Parity pins: see the test suite (tree exactness against brute-force MAP,
  * syndrome-sign symmetry, octonion identities, the printed d=2 noise form).
@@ -342,6 +347,142 @@ int orc_decode(int64_t n, int64_t m, int64_t n_edges, const int64_t *edge_cn,
     *conv_out = converged;
     free(l_vc);
     free(m_cv);
+    free_adj(&cn);
+    free_adj(&vn);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Layered schedule (extension; the paper decodes with flooding)            */
+/* ------------------------------------------------------------------------ */
+
+/* Sum-product decoding with the checks split into layers, layer[c] in
+ * [0, n_layers). Iteration t visits layers 0, 1, ..., n_layers-1; for the
+ * checks of layer l:
+ *   L_vc = clip(Q_v + sum_{c' != c} m_c'v)   over the messages as they stand
+ *          when layer l starts (edges of earlier layers already hold their
+ *          iteration-t messages, edges of this and later layers still hold
+ *          those of t-1; all messages start at 0);
+ *   m_cv = the check rule of Step 2 on those L_vc, for every edge of the
+ *          layer, written only after all of the layer's m_cv are computed.
+ * After the last layer L_v = Q_v + sum_c m_cv gives the decisions, and the
+ * stop test follows the same rule as orc_decode. With one layer this is
+ * exactly orc_decode (same sums in the same order). */
+int orc_decode_layered(int64_t n, int64_t m, int64_t n_edges, const int64_t *edge_cn,
+                       const int64_t *edge_vn, const double *q, const uint8_t *syn,
+                       int n_layers, const int32_t *layer, int max_iter, int et_start,
+                       double clip, double xmin, double *post, uint8_t *chat,
+                       int32_t *iters_out, int32_t *conv_out)
+{
+    adj_t cn, vn;
+    if (n_layers < 1)
+        return -1;
+    for (int64_t c = 0; c < m; c++)
+        if (layer[c] < 0 || layer[c] >= n_layers)
+            return -1;
+    if (build_adj(m, n_edges, edge_cn, &cn))
+        return -1;
+    if (build_adj(n, n_edges, edge_vn, &vn)) {
+        free_adj(&cn);
+        return -1;
+    }
+    size_t ne = (size_t)(n_edges > 0 ? n_edges : 1);
+    double *l_vc = (double *)malloc(ne * sizeof(double));
+    double *m_cv = (double *)calloc(ne, sizeof(double));
+    double *m_new = (double *)malloc(ne * sizeof(double));
+    if (!l_vc || !m_cv || !m_new) {
+        free(l_vc);
+        free(m_cv);
+        free(m_new);
+        free_adj(&cn);
+        free_adj(&vn);
+        return -1;
+    }
+    for (int64_t v = 0; v < n; v++) {
+        post[v] = q[v];
+        chat[v] = (uint8_t)(post[v] < 0.0);
+    }
+
+    int t = 0;
+    int converged = 0;
+    for (;;) {
+        int test = (t == max_iter) || (t >= 1 && t >= et_start);
+        if (test) {
+            int ok = 1;
+            for (int64_t c = 0; c < m && ok; c++) {
+                unsigned par = syn[c] & 1u;
+                for (int64_t k = cn.ptr[c]; k < cn.ptr[c + 1]; k++)
+                    par ^= chat[edge_vn[cn.edges[k]]];
+                if (par)
+                    ok = 0;
+            }
+            if (ok) {
+                converged = 1;
+                break;
+            }
+        }
+        if (t == max_iter)
+            break;
+        t++;
+
+        for (int l = 0; l < n_layers; l++) {
+            /* variable-to-check messages of the layer's edges */
+            for (int64_t c = 0; c < m; c++) {
+                if (layer[c] != l)
+                    continue;
+                for (int64_t k = cn.ptr[c]; k < cn.ptr[c + 1]; k++) {
+                    int64_t e = cn.edges[k];
+                    int64_t v = edge_vn[e];
+                    double ext = q[v];
+                    for (int64_t k2 = vn.ptr[v]; k2 < vn.ptr[v + 1]; k2++)
+                        if (vn.edges[k2] != e)
+                            ext += m_cv[vn.edges[k2]];
+                    l_vc[e] = clip_msg(ext, clip);
+                }
+            }
+            /* check-to-variable messages of the layer (Step 2) */
+            for (int64_t c = 0; c < m; c++) {
+                if (layer[c] != l)
+                    continue;
+                double ssign = (syn[c] & 1u) ? -1.0 : 1.0;
+                for (int64_t k = cn.ptr[c]; k < cn.ptr[c + 1]; k++) {
+                    int64_t e = cn.edges[k];
+                    double sign = ssign;
+                    double sum = 0.0;
+                    for (int64_t k2 = cn.ptr[c]; k2 < cn.ptr[c + 1]; k2++) {
+                        if (k2 == k)
+                            continue;
+                        double lv = l_vc[cn.edges[k2]];
+                        sign *= sgn(lv);
+                        sum += orc_phi(fmax(fabs(lv), xmin));
+                    }
+                    m_new[e] = clip_msg(sign * orc_phi(fmax(sum, xmin)), clip);
+                }
+            }
+            /* commit the layer */
+            for (int64_t c = 0; c < m; c++) {
+                if (layer[c] != l)
+                    continue;
+                for (int64_t k = cn.ptr[c]; k < cn.ptr[c + 1]; k++)
+                    m_cv[cn.edges[k]] = m_new[cn.edges[k]];
+            }
+        }
+
+        /* posteriors and decisions (Steps 3-4) */
+        for (int64_t v = 0; v < n; v++) {
+            double total = q[v];
+            for (int64_t k = vn.ptr[v]; k < vn.ptr[v + 1]; k++)
+                total += m_cv[vn.edges[k]];
+            post[v] = total;
+            chat[v] = (uint8_t)(total < 0.0);
+        }
+    }
+
+    *iters_out = t;
+    *conv_out = converged;
+    free(l_vc);
+    free(m_cv);
+    free(m_new);
     free_adj(&cn);
     free_adj(&vn);
     return 0;
