@@ -61,6 +61,9 @@ def parse_args():
                     help="stream: host-enqueued passes, for profilers only (not a bench number)")
     ap.add_argument("--msg-format", choices=["fp32", "fp16", "int8"], default="fp32",
                     help="storage of edge messages (arithmetic stays FP32)")
+    ap.add_argument("--schedule", choices=["flooding", "layered"], default="flooding")
+    ap.add_argument("--layers", type=int, default=0,
+                    help="layered: row groups per iteration (0 = one per base row)")
     ap.add_argument("--study", choices=["fer", "batch", "serve"], default=None,
                     help="instead of the throughput line: FER per message format (fer), a "
                          "mixed-rate 256-frame batch (batch) or a serving-load sweep (serve)")
@@ -298,7 +301,10 @@ def run_ours(args, world, rank, local):
     n, k, F, B = code.n, code.k, args.frames, args.batches
     wm, wk = (code.m + 31) // 32, (k + 31) // 32
     params = q.qcldpc_params_init(launch_mode=1 if args.launch_mode == "stream" else 0,
-                                  msg_format={"fp32": 0, "fp16": 1, "int8": 2}[args.msg_format])
+                                  msg_format={"fp32": 0, "fp16": 1, "int8": 2}[args.msg_format],
+                                  schedule=1 if args.schedule == "layered" else 0,
+                                  layers=args.layers)
+    layered = args.schedule == "layered"
 
     # --- seeded inputs, resident in HBM before timing
     host = []
@@ -380,8 +386,10 @@ def run_ours(args, world, rank, local):
         loop_passes.append(int(its.max()) + 1)
     frames_total = B * F
     fer = frame_err / frames_total
-    # per step: llr + init + final, and check pass + control + variable pass per loop pass
-    launches = sum(3 + 3 * loop_passes[s % B] for s in range(args.steps))
+    # per step: llr + init + final, and per loop pass check pass + control +
+    # variable pass (flooding) or test pass + control + 2 per row group (layered)
+    per_pass = 2 + 2 * (args.layers or d["mb"]) if layered else 3
+    launches = sum(3 + per_pass * loop_passes[s % B] for s in range(args.steps))
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host
     stage = {"x": torch.empty(F * n, dtype=torch.float32, device=dev),
@@ -421,8 +429,13 @@ def run_ours(args, world, rank, local):
     h2d = 2 * F * n * 4 + F * wm * 4
     d2h = F * wk * 4 + 2 * F * 4
 
-    # --- roofline of the dominant pass (replayed with the decode's launch shape)
-    q.qcldpc_decode(code, llr, batches[0]["syn"], F, args.max_iter, params, batches[0]["keys"],
+    # --- roofline of the dominant pass (replayed with the flooding decode's
+    # launch shape; a layered run replays the flooding passes of the same batch)
+    rparams = params
+    if layered:
+        rparams = q.qcldpc_params_init(msg_format=params.msg_format)
+        ws_bytes = q.qcldpc_decode_workspace(code, F, rparams)
+    q.qcldpc_decode(code, llr, batches[0]["syn"], F, args.max_iter, rparams, batches[0]["keys"],
                     batches[0]["conv"], batches[0]["iters"], ws, ws_bytes, stream)
     cn_ms, vn_ms = q.qcldpc_time_passes(code, F, ws, ws_bytes, args.reps, stream)
     col_count = np.bincount(d["col"], minlength=d["nb"])
@@ -460,6 +473,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "msg_format": args.msg_format,
+        "schedule": args.schedule if not layered else f"layered, {args.layers or d['mb']} row groups",
         "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "k": k, "snr": args.snr,
                    "frames_per_step": F, "distinct_frames": frames_total,
                    "max_iter": args.max_iter, "stop_test": "after every iteration",

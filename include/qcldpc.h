@@ -149,7 +149,14 @@ typedef struct qcldpc_params {
                             t >= et_start, and always after the last
                             iteration (delayed early termination, Sec. IV-A).
                             Default 1 */
-    int32_t schedule;    /* 0 = flooding (the only schedule of this build) */
+    int32_t schedule;    /* 0 = flooding (Algorithm 1, default); 1 = layered:
+                            the base rows are split into `layers` contiguous
+                            groups (row r in group floor(r * layers / mb)),
+                            visited in order within an iteration; a group's
+                            messages are computed from the state at the
+                            group's start and its posteriors updated before
+                            the next group (an extension of the paper's
+                            flooding decoder). Pools accept flooding only */
     int32_t msg_format;  /* storage of the check-to-variable messages, all
                             arithmetic FP32: 0 = FP32 (default), 1 = FP16
                             (round to nearest), 2 = int8 codes q with
@@ -164,6 +171,9 @@ typedef struct qcldpc_params {
                             cannot look inside conditional graphs. Default 0 */
     float msg_step;      /* int8 quantum in natural-LLR units; 0 (default)
                             means clip / 127. Ignored for other formats */
+    int32_t layers;      /* layered schedule: number of row groups, 1..mb;
+                            0 (default) = one group per base row. Ignored by
+                            flooding. layers = 1 computes what flooding does */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);

@@ -47,6 +47,7 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->soft_output = 0;
     p->launch_mode = 0;
     p->msg_step = 0.0f;
+    p->layers = 0;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
@@ -192,6 +193,7 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
             if (circ_col[h] != T.hcol_base[s]) continue;
             T.cols[pos].shift = circ_shift[h];
             T.cols[pos].id = hid[h];
+            T.col_row[pos] = (int16_t)circ_row[h];
             pos++;
         }
     }

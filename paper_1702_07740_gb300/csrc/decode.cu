@@ -115,7 +115,8 @@ struct Work {
     int32_t *active;       // [F]
     int32_t *fail;         // [F] stop-test failures of the current pass
     int32_t *err;          // device error word (a bounded wait gave up)
-    void *msg;             // [F][n_h][Z] messages in the storage format fmt
+    void *msg;             // [F][n_h][Z] messages in the storage format fmt (layered:
+                           // two such buffers msg_buf elements apart, by iteration parity)
     float *L;              // [F][n_hcols][2Z]
     float *phiq;           // [F][n_d1][Z]
     uint32_t *bits;        // [2][F][n_d1][ZW]
@@ -124,7 +125,17 @@ struct Work {
     int32_t n_frames, max_iter, et_start, soft, ZW, fmt;
     float clip, xmin;      // base-2 units
     float qstep, qinv;     // int8 message quantum and its inverse (base-2 units)
+    int64_t msg_buf;       // layered: elements per message buffer; 0 for flooding
+    int32_t layered;       // schedule: 0 flooding, 1 layered
+    int32_t ngroups;       // layered: row groups per iteration
+    int32_t pass;          // check-pass kind (kPassFlood, kPassTest, kPassGroup)
+    int32_t lrow0, lrows;  // kPassGroup and the group's posterior update: its base rows
 };
+// Kinds of check pass. kPassFlood: flooding iteration t (stop test of t-1
+// when due, then the update). kPassTest: the stop test of iteration t-1
+// alone, when due (layered). kPassGroup: the update of one row group for the
+// iteration the control step just counted on (layered, no test).
+enum CnPass { kPassFlood = 0, kPassTest = 1, kPassGroup = 2 };
 static_assert(sizeof(Work) <= sizeof(((qcldpc_code *)nullptr)->last_work), "Work too large");
 
 // ---------------------------------------------------------------- Phi
@@ -297,7 +308,8 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
     const int rp = T.row_ptr[r];
     const int deg = T.row_ptr[r + 1] - rp;
     const int nh = T.row_nh[r];
-    M *msg = static_cast<M *>(W.msg) + (size_t)f * T.n_h * Z;
+    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
+    M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
     const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
     const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
     const size_t bstride = (size_t)T.n_d1 * ZW;
@@ -322,7 +334,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
                 if (k < nh) {
                     const float lv = L[oa + i];
                     par ^= fbits(lv);
-                    const float d = lv - (read_msg ? Codec<M>::dec(msg[ob + i], W) : 0.0f);
+                    const float d = lv - (read_msg ? Codec<M>::dec(msg_rd[ob + i], W) : 0.0f);
                     phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
                     sg[k] = fbits(d);
                 } else {
@@ -477,7 +489,9 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     int *s_off = reinterpret_cast<int *>(smem + 16);  // per staged row: start of its data
     float *stage = reinterpret_cast<float *>(smem + kSmemHeader);
     const size_t bstride = (size_t)T.n_d1 * ZW;
-    M *msg = static_cast<M *>(W.msg) + (size_t)f * T.n_h * Z;
+    // messages of iteration t-1 (read) and t (written); one buffer when flooding
+    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
+    M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
 
     // Thread 0: arm the barrier, publish each staged row's read offset
     // (row slot * kStage + 16-byte remainder), then issue the copies.
@@ -511,7 +525,7 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
         if (kReadMsg) {
 #pragma unroll
             for (int k = 0; k < NH; k++)
-                add(msg + T.row_off_b[rp + k] + i0, kTile, (int)sizeof(M), kStage);
+                add(msg_rd + T.row_off_b[rp + k] + i0, kTile, (int)sizeof(M), kStage);
         }
         if (kUpdate) {
 #pragma unroll
@@ -753,11 +767,19 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kern
     extern __shared__ __align__(128) unsigned char smem[];
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
-    const int r = T.row_order[blockIdx.y];
-    const int t = W.t[f];
-    const int mode = t > W.max_iter ? kTestOnly
-                     : t == 1       ? kFirst
-                     : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
+    const bool group = W.pass == kPassGroup;
+    const int r = group ? W.lrow0 + (int)blockIdx.y : T.row_order[blockIdx.y];
+    const int t = W.t[f] - (group ? 1 : 0);
+    int mode = t > W.max_iter ? kTestOnly
+               : t == 1       ? kFirst
+               : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
+    if (W.pass == kPassTest) {
+        if (mode != kSteadyTest && mode != kTestOnly) return;  // no test due
+        mode = kTestOnly;
+    } else if (group) {
+        if (mode == kTestOnly) return;
+        if (mode == kSteadyTest) mode = kSteady;
+    }
     const int nh = T.row_nh[r];
     const int nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
     bool bad;
@@ -865,6 +887,53 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     }
 }
 
+// Layered schedule, posterior update of one row group: for every heavy
+// variable v, L_v += sum over the group's circulants of v's column of
+// (m_cv(t) - m_cv(t-1)), read at (j - s) mod Z from the two message buffers
+// (m(t-1) = 0 at t = 1). t is the iteration the group pass just computed.
+template <typename M>
+__global__ void __launch_bounds__(kThreads) lvn_kernel(const __grid_constant__ Table T,
+                                                       const __grid_constant__ Work W) {
+    const int f = blockIdx.z;
+    if (W.active[f] == 0) return;
+    const int t = W.t[f] - 1;
+    const int Z = T.Z;
+    const int hc = blockIdx.y;
+    const int j0 = blockIdx.x * (kThreads * kVnVpt) + threadIdx.x;
+    const M *__restrict__ mnew = static_cast<const M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
+    const M *__restrict__ mold = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
+    float d[kVnVpt];
+#pragma unroll
+    for (int u = 0; u < kVnVpt; u++) d[u] = 0.0f;
+    bool touched = false;
+    const int ce = T.col_ptr[hc + 1];
+    for (int k = T.col_ptr[hc]; k < ce; k++) {
+        const int row = T.col_row[k];
+        if (row < W.lrow0 || row >= W.lrow0 + W.lrows) continue;  // uniform
+        touched = true;
+        const qc::ColEnt e = T.cols[k];
+        const M *__restrict__ nk = mnew + e.id * Z;
+        const M *__restrict__ ok = mold + e.id * Z;
+#pragma unroll
+        for (int u = 0; u < kVnVpt; u++) {
+            int idx = j0 + u * kThreads - e.shift;
+            if (idx < 0) idx += Z;
+            d[u] += Codec<M>::dec(nk[idx], W) - (t > 1 ? Codec<M>::dec(ok[idx], W) : 0.0f);
+        }
+    }
+    if (!touched) return;
+    float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+#pragma unroll
+    for (int u = 0; u < kVnVpt; u++) {
+        const int j = j0 + u * kThreads;
+        if (j < Z) {
+            const float lvj = L[j] + d[u] + 0.0f;  // -0 -> +0
+            L[j] = lvj;
+            L[j + Z] = lvj;
+        }
+    }
+}
+
 // Outputs: packed key bits C_v (v < k) and, for soft output, every posterior.
 __global__ void __launch_bounds__(kThreads) final_kernel(const __grid_constant__ Table T,
                                                          const __grid_constant__ Work W) {
@@ -939,7 +1008,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 size_t msg_elem_size(int fmt) { return fmt == 2 ? 1 : fmt == 1 ? 2 : 4; }
 
-Layout layout_of(const Table &T, int F, bool soft, int fmt) {
+Layout layout_of(const Table &T, int F, bool soft, int fmt, bool layered = false) {
     Layout o;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -952,7 +1021,7 @@ Layout layout_of(const Table &T, int F, bool soft, int fmt) {
     o.err = take(sizeof(int32_t));
     o.active = take(sizeof(int32_t) * F);
     o.fail = take(sizeof(int32_t) * F);
-    o.msg = take(msg_elem_size(fmt) * (F * T.n_h * Z + kSlack));
+    o.msg = take(msg_elem_size(fmt) * ((layered ? 2 : 1) * F * T.n_h * Z + kSlack));
     o.L = take(sizeof(float) * (F * T.n_hcols * 2 * Z + kSlack));
     o.phiq = take(sizeof(float) * (F * T.n_d1 * Z + kSlack));
     o.bits = take(sizeof(uint32_t) * (2 * F * T.n_d1 * ZW + kSlack));
@@ -984,6 +1053,19 @@ void *cn_tma_kernel_for(int maxdeg, int fmt) {
     if (fmt == 1) return cn_tma_kernel_for_fmt<__half>(maxdeg);
     if (fmt == 2) return cn_tma_kernel_for_fmt<int8_t>(maxdeg);
     return cn_tma_kernel_for_fmt<float>(maxdeg);
+}
+
+void *lvn_kernel_for(int fmt) {
+    if (fmt == 1) return (void *)lvn_kernel<__half>;
+    if (fmt == 2) return (void *)lvn_kernel<int8_t>;
+    return (void *)lvn_kernel<float>;
+}
+
+// Base rows [r0, r1) of row group g when mb rows form G groups: row r is in
+// group floor(r * G / mb).
+void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
+    *r0 = (g * T.mb + G - 1) / G;
+    *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
 void *vn_kernel_for(int fmt) {
@@ -1064,7 +1146,9 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
 }
 
-// Loop body of the decode graph: check pass -> control -> variable pass.
+// Loop body of the decode graph. Flooding: check pass -> control ->
+// variable pass. Layered: stop-test pass -> control -> for every row group,
+// its check pass -> its posterior update.
 cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
                           cudaGraphConditionalHandle handle) {
     const int F = w0.n_frames;
@@ -1074,6 +1158,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
     cudaGraphNode_t n_cn, n_ctrl, n_vn;
     const CnLaunch cl = cn_launch(T, F, w0.fmt);
     cudaError_t err;
+    if (w0.layered) wcopy.pass = kPassTest;
     if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, dim3(kThreads), args,
                           cl.smem)) != cudaSuccess)
         return err;
@@ -1081,8 +1166,27 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
     if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                           dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
         return err;
-    return add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
-                      dim3(kThreads), args);
+    if (!w0.layered)
+        return add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
+                          dim3(kThreads), args);
+    cudaGraphNode_t prev = n_ctrl;
+    for (int g = 0; g < w0.ngroups; g++) {
+        Work wg = w0;
+        wg.pass = kPassGroup;
+        group_rows(T, w0.ngroups, g, &wg.lrow0, &wg.lrows);
+        wg.lrows -= wg.lrow0;
+        void *gargs[] = {&tcopy, &wg};
+        dim3 grid = cl.grid;
+        grid.y = (unsigned)wg.lrows;
+        cudaGraphNode_t a, b;
+        if ((err = add_kernel(&a, body, &prev, 1, cl.func, grid, dim3(kThreads), gargs,
+                              cl.smem)) != cudaSuccess ||
+            (err = add_kernel(&b, body, &a, 1, lvn_kernel_for(w0.fmt), vn_grid(T, F),
+                              dim3(kThreads), gargs)) != cudaSuccess)
+            return err;
+        prev = b;
+    }
+    return cudaSuccess;
 }
 
 // Build and instantiate the decode graph for one argument set.
@@ -1134,6 +1238,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
     const CnLaunch cl = cn_launch(T, F, w.fmt);
     Table tcopy = T;
     Work wcopy = w;
+    if (w.layered) wcopy.pass = kPassTest;
     void *args[] = {&tcopy, &wcopy};
     cudaGraphConditionalHandle none = 0;
     cudaError_t err = cudaGetLastError();
@@ -1141,8 +1246,21 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
-        if (t <= w.max_iter)
+        if (t <= w.max_iter && !w.layered)
             err = cudaLaunchKernel(vn_kernel_for(w.fmt), vn_grid(T, F), dim3(kThreads), args, 0, stream);
+        for (int g = 0; t <= w.max_iter && w.layered && g < w.ngroups && err == cudaSuccess; g++) {
+            Work wg = w;
+            wg.pass = kPassGroup;
+            group_rows(T, w.ngroups, g, &wg.lrow0, &wg.lrows);
+            wg.lrows -= wg.lrow0;
+            void *gargs[] = {&tcopy, &wg};
+            dim3 grid = cl.grid;
+            grid.y = (unsigned)wg.lrows;
+            err = cudaLaunchKernel(cl.func, grid, dim3(kThreads), gargs, cl.smem, stream);
+            if (err == cudaSuccess)
+                err = cudaLaunchKernel(lvn_kernel_for(w.fmt), vn_grid(T, F), dim3(kThreads), gargs,
+                                       0, stream);
+        }
         if (err == cudaSuccess) err = cudaGetLastError();
     }
     if (err == cudaSuccess) {
@@ -1166,10 +1284,12 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     const bool soft = post != nullptr;
     if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode: n_frames must be in [0, 65535]");
     if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
-    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format < 0 || p.msg_format > 2 ||
-        !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1))
+    if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
+        p.msg_format > 2 || !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1) ||
+        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)))
         return fail(QCLDPC_E_INVAL,
-                    "decode: unsupported option (phi_floor > 0, flooding, msg_format 0..2, msg_step >= 0)");
+                    "decode: unsupported option (phi_floor > 0, schedule 0..1, layers 0..mb, "
+                    "msg_format 0..2, msg_step >= 0)");
     if (soft && p.soft_output != 1)
         return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
     if (F == 0) return QCLDPC_OK;
@@ -1185,7 +1305,8 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode: current device differs from the code's device");
 
     const Table &T = code->tab;
-    const Layout lo = layout_of(T, F, soft, p.msg_format);
+    const bool layered = p.schedule == 1;
+    const Layout lo = layout_of(T, F, soft, p.msg_format, layered);
     if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
     char *base = static_cast<char *>(ws);
     Work w;
@@ -1221,6 +1342,11 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
         const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;
         w.qstep = step * kLog2e;
         w.qinv = 1.0f / w.qstep;
+    }
+    if (layered) {
+        w.layered = 1;
+        w.ngroups = p.layers > 0 ? p.layers : T.mb;
+        w.msg_buf = (int64_t)F * T.n_h * T.Z;
     }
 
     std::lock_guard<std::mutex> lock(code->mu);
@@ -1275,7 +1401,7 @@ extern "C" size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
     const bool soft = p && p->soft_output == 1;
     const int fmt = p ? p->msg_format : 0;
     if (fmt < 0 || fmt > 2) return 0;
-    return layout_of(code->tab, n_frames, soft, fmt).total;
+    return layout_of(code->tab, n_frames, soft, fmt, p && p->schedule == 1).total;
 }
 
 extern "C" int qcldpc_decode(const qcldpc_code *code, const float *llr_dev,
@@ -1314,6 +1440,7 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
         return fail(QCLDPC_E_INVAL, "time_passes: no decode ran on this workspace with this frame count");
     Work w;
     std::memcpy(&w, code->last_work, sizeof(w));
+    if (w.layered) return fail(QCLDPC_E_INVAL, "time_passes: the last decode was layered (flooding only)");
     const Layout lo = layout_of(code->tab, n_frames, code->last_soft != 0, w.fmt);
     if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "time_passes: workspace too small");
     if (w.max_iter < 2) w.max_iter = 2;  // replays run as iteration 2: a full update
@@ -1813,7 +1940,8 @@ extern "C" int qcldpc_decode_noalloc(const qcldpc_code *code, const float *llr_d
     using namespace qc;
     if (!code) return fail(QCLDPC_E_INVAL, "decode_noalloc: code is NULL");
     if (n_frames < 0) return fail(QCLDPC_E_INVAL, "decode_noalloc: negative frame count");
-    const size_t need = layout_of(code->tab, n_frames, false, p ? p->msg_format : 0).total;
+    const size_t need =
+        layout_of(code->tab, n_frames, false, p ? p->msg_format : 0, p && p->schedule == 1).total;
     if (need > kNoallocScratchBytes)
         return fail(QCLDPC_E_UNSUPPORTED,
                     "decode_noalloc: this code and frame count need " + std::to_string(need) +

@@ -59,6 +59,7 @@ struct Table {
     int32_t row_off_a[kMaxCirc];
     int32_t row_off_b[kMaxCirc];
     ColEnt cols[kMaxCirc];
+    int16_t col_row[kMaxCirc];          // base row of each cols[] entry
     int32_t d1_shift[kMaxCirc];
     int16_t d1_row[kMaxCirc];
     int16_t d1_col[kMaxCirc];

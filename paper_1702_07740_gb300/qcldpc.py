@@ -51,6 +51,7 @@ class qcldpc_params(ctypes.Structure):
         ("soft_output", ctypes.c_int32),
         ("launch_mode", ctypes.c_int32),
         ("msg_step", ctypes.c_float),
+        ("layers", ctypes.c_int32),
     ]
 
 

@@ -33,6 +33,7 @@ def test_params_defaults():
     assert p.clip == pytest.approx(15.0)
     assert p.phi_floor == pytest.approx(1e-6)
     assert p.et_start == 1 and p.schedule == 0 and p.msg_format == 0 and p.soft_output == 0
+    assert p.layers == 0
 
 
 def test_code_info_of_the_rate002_protograph():
@@ -70,3 +71,14 @@ def test_workspace_size_grows_with_frames_and_soft_output():
     assert 0 < w1 < w16 and ws > w1
     # messages of 119 heavy circulants dominate: >= 119 * Z floats per frame
     assert w16 >= 16 * 119 * 512 * 4
+
+
+def test_layered_workspace_holds_two_message_buffers():
+    """The layered schedule keeps the messages of iterations t-1 and t."""
+    d = synth.rate002_code(512)
+    code = q.create_code_from(d)
+    flood = q.qcldpc_decode_workspace(code, 3)
+    lay = q.qcldpc_decode_workspace(code, 3, q.qcldpc_params_init(schedule=1))
+    n_h = 119
+    assert lay - flood >= 3 * n_h * 512 * 4 - 256
+    assert lay - flood <= 3 * n_h * 512 * 4 + 256
