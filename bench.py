@@ -64,7 +64,7 @@ def parse_args():
     ap.add_argument("--schedule", choices=["flooding", "layered"], default="flooding")
     ap.add_argument("--layers", type=int, default=0,
                     help="layered: row groups per iteration (0 = one per base row)")
-    ap.add_argument("--study", choices=["fer", "batch", "serve"], default=None,
+    ap.add_argument("--study", choices=["fer", "batch", "serve", "schedule", "et"], default=None,
                     help="instead of the throughput line: FER per message format (fer), a "
                          "mixed-rate 256-frame batch (batch) or a serving-load sweep (serve)")
     ap.add_argument("--study-frames", type=int, default=2000, help="fer: frames per SNR")

@@ -9,6 +9,10 @@
   and 0.10, each at n = 10^5, 4*10^5 and 10^6) decoded together by frame
   pools stepped in one graph launch (FP16 and FP32 messages), against the
   plain FP32 decoder run one frame at a time and one code at a time.
+* ``schedule``: the library's autotuner (flooding vs layered with 2, 7 and
+  mb row groups) on a 16-frame sample of each FER operating point.
+* ``et``: delayed early termination, an SNR -> et_start table built from
+  sample frames, against the stop test from iteration 1.
 * ``serve``: Poisson arrivals of frames of the same mix into the
   continuous-batching server (FP16 messages) at offered loads from 10 % to
   120 % of its measured capacity; p50/p99 frame latency and served Mbit/s,
@@ -415,7 +419,79 @@ def study_serve(args):
               "vs_fifo": paired(ferr, err)})
 
 
+# ---------------------------------------------------------------- schedule
+
+def study_schedule(args):
+    """The autotuner on a sample batch of each FER operating point: the time
+    each candidate schedule needs to decode the batch, and its choice."""
+    F = 16
+    for si, item in enumerate(args.fer_points.split(",")):
+        cname, snr = item.split(":")
+        snr = float(snr)
+        mk, Z, label = FER_CODES[cname]
+        code = q.create_code_from(mk(Z))
+        llr, syn, key = make_frames(code, F, snr, seed=9_000_000 + si)
+        lay = q.qcldpc_params_init(schedule=1)
+        ws_bytes = q.qcldpc_decode_workspace(code, F, lay)
+        ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+        wk = (code.k + 31) // 32
+        keys = torch.empty(F * wk, dtype=torch.int32, device="cuda")
+        conv = torch.empty(F, dtype=torch.int32, device="cuda")
+        its = torch.empty(F, dtype=torch.int32, device="cuda")
+        best, times = q.qcldpc_autotune(code, llr, syn, F, args.max_iter, None, keys, conv, its,
+                                        ws, ws_bytes, reps=3)
+        emit({"study": "schedule", "code": f"{label}, Z={Z}, n={code.n}", "snr": snr,
+              "frames": F, "max_iter": args.max_iter,
+              "ms_per_batch": times,
+              "mbps": {k: F * code.n / (v * 1e-3) / 1e6 for k, v in times.items()},
+              "chosen": {"schedule": "layered" if best.schedule else "flooding",
+                         "layers": best.layers}})
+
+
+# --------------------------------------------------------------------- et
+
+def study_et(args):
+    """Delayed early termination (Sec. IV-A): build the SNR -> et_start table
+    from a 16-frame sample per SNR, then decode 64 other frames per SNR with
+    the test from iteration 1 and from the table's start."""
+    from paper_1702_07740_gb300 import et_lut
+    Z = 20000
+    code = q.create_code_from(synth.rate002_code(Z))
+    wk = (code.k + 31) // 32
+    snrs = [0.029, 0.1, 0.13, 0.16, 0.2]
+    sample = {}
+    for i, snr in enumerate(snrs):
+        llr, syn, _ = make_frames(code, 16, snr, seed=9_100_000 + i)
+        sample[snr] = (llr, syn, 16)
+    lut = et_lut.build(code, sample, args.max_iter)
+    del sample
+    F = 64
+    for i, snr in enumerate(snrs):
+        llr, syn, key = make_frames(code, F, snr, seed=9_200_000 + i)
+        out = {}
+        for name, et in (("test_from_1", 1), ("table", lut.et_start_for(snr))):
+            p = q.qcldpc_params_init()
+            p.et_start = et
+            dec = q.Decoder(code, F, p)
+            dec.decode(llr, syn, args.max_iter)  # warm-up: graph instantiation
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            dec.decode(llr, syn, args.max_iter)
+            e1.record()
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            err = (dec.keys.view(F, wk) != key).any(1).cpu().numpy()
+            out[name] = {"et_start": et, "mbps": F * code.n / sec / 1e6,
+                         "mean_iters": float(dec.iters.float().mean()),
+                         "converged": int(dec.converged.sum()), "errors": int(err.sum()),
+                         "keys": dec.keys.clone()}
+        same = bool(torch.equal(out["test_from_1"].pop("keys"), out["table"].pop("keys")))
+        emit({"study": "et", "code": f"rate 0.02, Z={Z}, n={code.n}", "snr": snr, "frames": F,
+              "max_iter": args.max_iter, "same_keys": same, **out})
+
+
 def run(args):
     torch.cuda.set_device(0)
     q.load()
-    {"fer": study_fer, "batch": study_batch, "serve": study_serve}[args.study](args)
+    {"fer": study_fer, "batch": study_batch, "serve": study_serve,
+     "schedule": study_schedule, "et": study_et}[args.study](args)

@@ -275,6 +275,33 @@ int qcldpc_pool_collect(qcldpc_pool *pool, int n, const int32_t *slots_dev,
                         qcldpc_stream_t stream);
 
 /*
+ * Schedule autotuner; an extension (the paper fixes flooding). Decodes the
+ * caller's sample batch once per candidate schedule: flooding, then layered
+ * with 2, 7 and mb row groups (those in [1, mb], without repeats). Every
+ * other option comes from p. Each candidate runs once untimed (its graph is
+ * instantiated), then `reps` times between CUDA events on `stream`; the
+ * fastest candidate's options are written to *best. What is timed is the
+ * time to decode the sample, including the iterations each schedule needs,
+ * so the sample should look like the frames to come (code, SNR, batch size).
+ *   llr_dev .. iters_dev   as qcldpc_decode; the outputs of the last sample
+ *                          decode are left there
+ *   workspace_dev          at least qcldpc_decode_workspace(code, n_frames,
+ *                          p with schedule = 1) bytes (the larger layout)
+ *   reps                   >= 1 timed decodes per candidate
+ *   best                   HOST qcldpc_params, written on success
+ *   times_ms               optional HOST float[4]: mean decode time per
+ *                          candidate (flooding, 2, 7, mb groups), NAN where
+ *                          a candidate was not tried
+ * Blocks the calling thread until the timings are known. Errors as
+ * qcldpc_decode.
+ */
+int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev, const uint32_t *syn_dev,
+                    int n_frames, int max_iter, const qcldpc_params *p,
+                    uint32_t *key_bits_dev, int32_t *converged_dev, int32_t *iters_dev,
+                    void *workspace_dev, size_t workspace_bytes, int reps,
+                    qcldpc_params *best, float *times_ms, qcldpc_stream_t stream);
+
+/*
  * Measurement helper; the paper has no counterpart. Replays the check-node
  * pass and then the variable-node pass of the decoder `reps` times each, with
  * the launch configuration qcldpc_decode uses, on the state a previous

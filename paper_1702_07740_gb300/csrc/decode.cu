@@ -1426,6 +1426,69 @@ extern "C" int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
                        (cudaStream_t)stream);
 }
 
+extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,
+                               const uint32_t *syn_dev, int n_frames, int max_iter,
+                               const qcldpc_params *p_in, uint32_t *key_bits_dev,
+                               int32_t *converged_dev, int32_t *iters_dev, void *workspace_dev,
+                               size_t workspace_bytes, int reps, qcldpc_params *best,
+                               float *times_ms, qcldpc_stream_t stream_) {
+    using namespace qc;
+    if (!code || !best || reps < 1 || n_frames < 1)
+        return fail(QCLDPC_E_INVAL, "autotune: bad argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    qcldpc_params base;
+    if (p_in) base = *p_in;
+    else qcldpc_params_init(&base);
+    const int mb = code->tab.mb;
+    const int want[4] = {0, 2, 7, mb};  // 0: flooding, else layered with that many groups
+    if (times_ms)
+        for (int i = 0; i < 4; i++) times_ms[i] = NAN;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t err;
+    if ((err = cudaEventCreate(&e0)) != cudaSuccess || (err = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(err, "autotune: cudaEventCreate");
+    }
+    int best_i = -1;
+    float best_ms = INFINITY;
+    int st = QCLDPC_OK;
+    for (int i = 0; i < 4 && st == QCLDPC_OK; i++) {
+        if (i > 0 && (want[i] > mb || (i == 3 && (mb == 2 || mb == 7)))) continue;
+        qcldpc_params p = base;
+        p.schedule = want[i] ? 1 : 0;
+        p.layers = want[i];
+        auto run = [&]() {
+            return decode_impl(code, llr_dev, syn_dev, n_frames, max_iter, &p, key_bits_dev,
+                               converged_dev, iters_dev, nullptr, workspace_dev, workspace_bytes,
+                               stream);
+        };
+        if ((st = run()) != QCLDPC_OK) break;  // untimed: graph instantiation
+        cudaEventRecord(e0, stream);
+        for (int r = 0; r < reps && st == QCLDPC_OK; r++) st = run();
+        cudaEventRecord(e1, stream);
+        if (st != QCLDPC_OK) break;
+        float ms = 0.0f;
+        if ((err = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (err = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            st = cuda_fail(err, "autotune: timing");
+            break;
+        }
+        ms /= (float)reps;
+        if (times_ms) times_ms[i] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_i = i;
+            *best = p;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != QCLDPC_OK) return st;
+    if (best_i < 0) return fail(QCLDPC_E_INVAL, "autotune: no candidate ran");
+    clear_error();
+    return QCLDPC_OK;
+}
+
 extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void *workspace_dev,
                                   size_t workspace_bytes, int reps, float *cn_ms, float *vn_ms,
                                   qcldpc_stream_t stream_) {

@@ -28,7 +28,7 @@ EXPORTED = [
     "qcldpc_syndrome", "qcldpc_bob_message_8d", "qcldpc_llr_8d",
     "qcldpc_bob_message", "qcldpc_llr",
     "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
-    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc",
+    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc", "qcldpc_autotune",
     "qcldpc_pool_workspace", "qcldpc_pool_create", "qcldpc_pool_destroy", "qcldpc_pool_state",
     "qcldpc_pool_load", "qcldpc_pool_step", "qcldpc_pools_step", "qcldpc_pool_collect",
     "qcldpc_last_error",
@@ -108,6 +108,10 @@ def load(build_if_missing: bool = True):
         lib.qcldpc_decode_noalloc.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
                                               vp, vp, vp, vp]
         lib.qcldpc_decode_noalloc.restype = i32
+        lib.qcldpc_autotune.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
+                                        vp, vp, vp, vp, sz, i32, ctypes.POINTER(qcldpc_params),
+                                        ctypes.POINTER(ctypes.c_float), vp]
+        lib.qcldpc_autotune.restype = i32
         lib.qcldpc_pool_workspace.argtypes = [vp, i32, ctypes.POINTER(qcldpc_params)]
         lib.qcldpc_pool_workspace.restype = sz
         lib.qcldpc_pool_create.argtypes = [vp, i32, i32, ctypes.POINTER(qcldpc_params), vp, sz, vp,
@@ -290,6 +294,26 @@ def qcldpc_time_passes(code: Code, n_frames: int, workspace_dev, workspace_bytes
                                    ctypes.byref(vn), _stream(stream))
     _check(st, "qcldpc_time_passes")
     return cn.value, vn.value
+
+
+AUTOTUNE_CANDIDATES = ("flooding", "layered 2 groups", "layered 7 groups", "layered mb groups")
+
+
+def qcldpc_autotune(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,
+                    params: qcldpc_params | None, key_bits_dev, converged_dev, iters_dev,
+                    workspace_dev, workspace_bytes: int, reps: int = 3, stream=None):
+    """Fastest schedule for the sample batch: (best params, {candidate: ms})."""
+    best = qcldpc_params()
+    times = (ctypes.c_float * 4)()
+    p = ctypes.byref(params) if params is not None else None
+    st = load().qcldpc_autotune(code.handle, _dev(llr_dev, 4, "llr_dev"), _dev(syn_dev, 4, "syn_dev"),
+                                int(n_frames), int(max_iter), p, _dev(key_bits_dev, 4, "key_bits_dev"),
+                                _dev(converged_dev, 4, "converged_dev"), _dev(iters_dev, 4, "iters_dev"),
+                                _dev(workspace_dev, None, "workspace"), int(workspace_bytes), int(reps),
+                                ctypes.byref(best), times, _stream(stream))
+    _check(st, "qcldpc_autotune")
+    return best, {name: times[i] for i, name in enumerate(AUTOTUNE_CANDIDATES)
+                  if times[i] == times[i]}
 
 
 def qcldpc_decode_noalloc(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,

@@ -154,3 +154,33 @@ def test_layered_rejects_bad_group_counts_and_pools():
             q.qcldpc_decode(code, x, s, 1, 5, params, dec.keys, dec.converged, dec.iters, buf, ws)
     with pytest.raises(q.QcldpcError):
         q.Pool(code, 2, 10, q.qcldpc_params_init(schedule=1))
+
+
+def test_autotune_picks_the_fastest_measured_schedule():
+    fr = make_frames(synth.rate002_code(512), 0.3, 8)
+    code = q.create_code_from(fr.code_dict)
+    llr = gpu_llr(fr)
+    lay = q.qcldpc_params_init(schedule=1)
+    ws_bytes = q.qcldpc_decode_workspace(code, fr.F, lay)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    wk = (code.k + 31) // 32
+    keys = torch.empty(fr.F * wk, dtype=torch.int32, device="cuda")
+    conv = torch.empty(fr.F, dtype=torch.int32, device="cuda")
+    its = torch.empty(fr.F, dtype=torch.int32, device="cuda")
+    syn = torch.from_numpy(synth.pack_bits(fr.syn).view(np.int32).reshape(-1)).cuda()
+    best, times = q.qcldpc_autotune(code, llr, syn, fr.F, 60, None, keys, conv, its, ws,
+                                    ws_bytes, reps=2)
+    assert set(times) == set(q.AUTOTUNE_CANDIDATES)  # mb = 49: all four candidates
+    assert all(t > 0 for t in times.values())
+    fastest = q.AUTOTUNE_CANDIDATES.index(min(times, key=times.get))
+    assert (best.schedule, best.layers) == [(0, 0), (1, 2), (1, 7), (1, 49)][fastest]
+    print("autotune ms:", {k: round(v, 3) for k, v in times.items()})
+    # the chosen options decode like that schedule
+    a = decode_soft(code, llr, fr.syn, fr.F, 60, schedule=best.schedule, layers=best.layers)
+    layer = oracle.row_layers(fr.code, best.layers) if best.schedule else None
+    for f in range(fr.F):
+        if layer is None:
+            _, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], 60)
+        else:
+            _, chat, it, cv = oracle.decode_layered(fr.code, fr.q64[f], fr.syn[f], 60, layer)
+        assert (a[2][f], a[1][f]) == (it, int(cv))
