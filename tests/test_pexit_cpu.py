@@ -1,0 +1,67 @@
+"""Pins of the protograph EXIT threshold tool (CPU).
+
+* J against a direct quadrature of the BIAWGN capacity (scipy), and J_inv;
+* regular (3,6) and (4,8) ensembles against their exact density-evolution
+  thresholds sigma* = 0.8809 and 0.8314 (Richardson and Urbanke); the
+  Gaussian approximation is known to be within about 1 % on these;
+* no threshold beats the Shannon limit of its rate;
+* the seeded codes' base matrices (rates 0.02, 0.05, 0.10).
+"""
+import numpy as np
+import pytest
+
+import synth
+from paper_1702_07740_gb300 import pexit
+
+integrate = pytest.importorskip("scipy.integrate")
+optimize = pytest.importorskip("scipy.optimize")
+
+
+def _capacity_quad(snr):
+    s2 = 1.0 / snr
+
+    def integrand(y):
+        p = np.exp(-(y - 1) ** 2 / (2 * s2)) / np.sqrt(2 * np.pi * s2)
+        return p * np.log2(1 + np.exp(-2 * y / s2))
+    v, _ = integrate.quad(integrand, -40 * np.sqrt(s2) + 1, 40 * np.sqrt(s2) + 1, limit=400)
+    return 1.0 - v
+
+
+@pytest.mark.parametrize("snr", [0.03, 0.3, 1.0, 4.0])
+def test_J_is_the_biawgn_capacity(snr):
+    assert pexit.biawgn_capacity(snr) == pytest.approx(_capacity_quad(snr), abs=2e-6)
+
+
+def test_J_inverse():
+    s = np.array([0.05, 0.5, 1.0, 2.0, 5.0, 10.0])
+    np.testing.assert_allclose(pexit.J_inv(pexit.J(s)), s, rtol=1e-4)
+    np.testing.assert_allclose(pexit.J_fast(s), pexit.J(s), atol=1e-6)
+
+
+@pytest.mark.parametrize("B, sigma_de, rtol", [([[3, 3]], 0.8809, 0.005), ([[4, 4]], 0.8314, 0.015)])
+def test_regular_ensembles_match_density_evolution(B, sigma_de, rtol):
+    th = pexit.threshold(np.array(B))
+    assert 1.0 / np.sqrt(th) == pytest.approx(sigma_de, rel=rtol)
+    assert not pexit.converges(np.array(B), th * 0.98)
+    assert pexit.converges(np.array(B), th * 1.02)
+
+
+def _shannon_snr(rate):
+    return optimize.brentq(lambda s: pexit.biawgn_capacity(s) - rate, 1e-4, 100.0)
+
+
+@pytest.mark.parametrize("mk, rate", [(synth.rate002_code, 0.02), (synth.rate005_code, 0.05),
+                                      (synth.rate010_code, 0.10)])
+def test_seeded_code_thresholds_respect_the_shannon_limit(mk, rate):
+    B = pexit.base_matrix(mk(8))
+    assert pexit.rate(B) == pytest.approx(rate)
+    th = pexit.threshold(B, hi=20.0)
+    assert th > _shannon_snr(rate)
+    print(f"rate {rate}: PEXIT threshold SNR {th:.4f}, Shannon limit {_shannon_snr(rate):.4f}")
+
+
+def test_base_matrix_counts_circulants():
+    B = pexit.base_matrix(synth.rate002_code(8))
+    assert B.shape == (49, 50)
+    assert B[:, 0].sum() == 60 and B[:, 1].sum() == 59
+    assert np.all(B[np.arange(48), np.arange(2, 50)] == 1)
