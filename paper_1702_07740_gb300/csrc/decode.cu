@@ -65,7 +65,7 @@ using qc::Table;
 // Launch shapes (overridable at build time for tuning sweeps). Defaults
 // from a sweep at Z = 20,000 with 16 frames on GB300.
 #ifndef QCLDPC_VN_VPT
-#define QCLDPC_VN_VPT 2
+#define QCLDPC_VN_VPT 3
 #endif
 #ifndef QCLDPC_VN_UNROLL
 #define QCLDPC_VN_UNROLL 6
@@ -84,6 +84,12 @@ constexpr int kTmaVpt = QCLDPC_CN_TVPT;
 // Resident blocks per SM the staged pass is compiled for (caps registers).
 #ifndef QCLDPC_CN_TMA_MINBLOCKS
 #define QCLDPC_CN_TMA_MINBLOCKS 5
+#endif
+// Programmatic dependent launch inside a flooding iteration: the control and
+// variable passes are scheduled while their predecessor drains and wait for
+// it on the device (griddepcontrol), hiding the launch gaps.
+#ifndef QCLDPC_PDL
+#define QCLDPC_PDL 1
 #endif
 // Evaluate a thread's checks two at a time in packed FP32x2 arithmetic.
 #ifndef QCLDPC_CN_PAIR
@@ -206,6 +212,14 @@ __device__ __forceinline__ float2 psi2(float2 y) {
     const float2 ta = __fmul2_rn(t, a);
     return make_float2(fmaxf(small.x, ta.x), fmaxf(small.y, ta.y));
 }
+
+// Programmatic dependent launch: let the next kernel of the graph be
+// scheduled now / wait until the previous kernel's results are visible.
+// Without a programmatic edge both are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 constexpr uint32_t kSign = 0x80000000u;
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
@@ -765,6 +779,7 @@ template <int MAXD, typename M>
 __global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kernel(const __grid_constant__ Table T,
                                                           const __grid_constant__ Work W) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_launch_dependents();  // the control step may be scheduled; it waits for this pass
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
     const bool group = W.pass == kPassGroup;
@@ -806,6 +821,8 @@ template <bool kInGraph>
 __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constant__ Work W,
                                                             cudaGraphConditionalHandle handle) {
     __shared__ int any;
+    pdl_wait();  // the check pass's flags are complete and visible
+    pdl_launch_dependents();
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
     const bool failed = *W.err != 0;  // a staged copy never completed: stop, flag -1
@@ -850,6 +867,7 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 template <typename M>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
                                                       const __grid_constant__ Work W) {
+    pdl_wait();  // the control step's flags are complete and visible
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;
     const int Z = T.Z;
@@ -1135,7 +1153,23 @@ void free_entry(GraphEntry &g) {
 
 cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep,
                        size_t ndep, void *func, dim3 grid, dim3 block, void **args,
-                       size_t smem = 0) {
+                       size_t smem = 0, bool programmatic = false) {
+    if (programmatic && QCLDPC_PDL && ndep == 1) {
+        // edge that fires when every block of the upstream kernel has
+        // triggered (or exited); the kernel waits for its completion itself
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = func;
+        np.kernel.gridDim = grid;
+        np.kernel.blockDim = block;
+        np.kernel.sharedMemBytes = (unsigned)smem;
+        np.kernel.kernelParams = args;
+        np.kernel.extra = nullptr;
+        cudaGraphEdgeData ed = {};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        return cudaGraphAddNode(node, g, dep, &ed, 1, &np);
+    }
     cudaKernelNodeParams kp = {};
     kp.func = func;
     kp.gridDim = grid;
@@ -1163,12 +1197,13 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
                           cl.smem)) != cudaSuccess)
         return err;
     void *ctrl_args[] = {&wcopy, &handle};
+    const bool pdl = !w0.layered;
     if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
-                          dim3(kCtrlThreads), ctrl_args)) != cudaSuccess)
+                          dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
         return err;
     if (!w0.layered)
         return add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
-                          dim3(kThreads), args);
+                          dim3(kThreads), args, 0, true);
     cudaGraphNode_t prev = n_ctrl;
     for (int g = 0; g < w0.ngroups; g++) {
         Work wg = w0;
