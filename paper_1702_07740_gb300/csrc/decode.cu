@@ -32,6 +32,15 @@
 //   vn_kernel   per heavy variable v: L_v = Q_v + sum over its ~60 circulants
 //               of m_cv, read at offsets (j - s) mod Z (coalesced, one wrap).
 // A last pass (t = max_iter + 1) runs cn_tma_kernel as a pure stop test.
+// Inside the decode graph the control and variable passes hang off
+// programmatic edges: they are scheduled while their predecessor drains and
+// wait for its results on the device.
+//
+// Layered schedule (an extension; schedule = 1): the base rows form G groups
+// visited in order. An iteration is a stop-test pass (cn_tma_kernel, test
+// only), the control kernel, then per group the group's check pass (messages
+// of iteration t written to the other of two buffers, next to those of t-1)
+// and lvn_kernel, which adds the group's message changes to the posteriors.
 //
 // All call arguments travel as one __grid_constant__ parameter (Work), so
 // they sit in the constant bank as warp-uniform operands; instantiated graphs
