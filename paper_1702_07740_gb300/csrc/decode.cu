@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 // Grid (tile, heavy column, frame). Lanes past the end of the column read
 // message padding (never stored); the channel LLRs, the caller's buffer, are
 // read only in range.
-template <typename M>
+template <typename M, int VPT>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
                                                       const __grid_constant__ Work W) {
     pdl_wait();  // the control step's flags are complete and visible
@@ -881,13 +881,13 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     if (W.active[f] == 0) return;
     const int Z = T.Z;
     const int hc = blockIdx.y;
-    const int j0 = blockIdx.x * (kThreads * kVnVpt) + threadIdx.x;
+    const int j0 = blockIdx.x * (kThreads * VPT) + threadIdx.x;
     const M *__restrict__ msg = static_cast<const M *>(W.msg) + (size_t)f * T.n_h * Z;
     const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
     float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
-    float acc[kVnVpt];
+    float acc[VPT];
 #pragma unroll
-    for (int u = 0; u < kVnVpt; u++) {
+    for (int u = 0; u < VPT; u++) {
         const int j = j0 + u * kThreads;
         acc[u] = j < Z ? __ldg(q + j) * kLog2e : 0.0f;
     }
@@ -897,14 +897,14 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
         const qc::ColEnt e = T.cols[k];
         const M *__restrict__ mk = msg + e.id * Z;
 #pragma unroll
-        for (int u = 0; u < kVnVpt; u++) {
+        for (int u = 0; u < VPT; u++) {
             int idx = j0 + u * kThreads - e.shift;
             if (idx < 0) idx += Z;
             acc[u] += Codec<M>::dec(mk[idx], W);
         }
     }
 #pragma unroll
-    for (int u = 0; u < kVnVpt; u++) {
+    for (int u = 0; u < VPT; u++) {
         const int j = j0 + u * kThreads;
         if (j < Z) {
             const float lvj = acc[u] + 0.0f;  // -0 -> +0: sgn(0) = +1 everywhere
@@ -1057,6 +1057,41 @@ Layout layout_of(const Table &T, int F, bool soft, int fmt, bool layered = false
     return o;
 }
 
+// Variable pass: kernel and grid. A thread sums VPT nodes; VPT is the
+// largest of 3, 2, 1 that still gives the grid 4 blocks per SM (wider tiles
+// cut per-node overhead; a small batch needs the narrower tiles' blocks).
+struct VnLaunch {
+    void *func;
+    dim3 grid;
+};
+
+template <typename M>
+void *vn_kernel_vpt(int vpt) {
+    if (vpt == 3) return (void *)vn_kernel<M, 3>;
+    if (vpt == 2) return (void *)vn_kernel<M, 2>;
+    return (void *)vn_kernel<M, 1>;
+}
+
+int sm_count();
+
+VnLaunch vn_launch(const Table &T, int F, int fmt) {
+    const int hc = std::max(T.n_hcols, 1);
+    const long long want = 4LL * sm_count();
+    int vpt = 1;
+    for (int v = 3; v >= 1; v--) {
+        const long long blocks = (long long)F * hc * ((T.Z + kThreads * v - 1) / (kThreads * v));
+        if (blocks >= want || v == 1) {
+            vpt = v;
+            break;
+        }
+    }
+    VnLaunch l;
+    l.grid = dim3((unsigned)((T.Z + kThreads * vpt - 1) / (kThreads * vpt)), (unsigned)hc, (unsigned)F);
+    l.func = fmt == 1 ? vn_kernel_vpt<__half>(vpt) : fmt == 2 ? vn_kernel_vpt<int8_t>(vpt)
+                                                             : vn_kernel_vpt<float>(vpt);
+    return l;
+}
+
 dim3 vn_grid(const Table &T, int F) {
     const int span = kThreads * kVnVpt;
     return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)std::max(T.n_hcols, 1), (unsigned)F);
@@ -1095,11 +1130,6 @@ void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
     *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
-void *vn_kernel_for(int fmt) {
-    if (fmt == 1) return (void *)vn_kernel<__half>;
-    if (fmt == 2) return (void *)vn_kernel<int8_t>;
-    return (void *)vn_kernel<float>;
-}
 
 template <typename M>
 void raise_smem_cap(int cap) {
@@ -1210,9 +1240,10 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
     if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                           dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
         return err;
-    if (!w0.layered)
-        return add_kernel(&n_vn, body, &n_ctrl, 1, vn_kernel_for(w0.fmt), vn_grid(T, F),
-                          dim3(kThreads), args, 0, true);
+    if (!w0.layered) {
+        const VnLaunch vl = vn_launch(T, F, w0.fmt);
+        return add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), args, 0, true);
+    }
     cudaGraphNode_t prev = n_ctrl;
     for (int g = 0; g < w0.ngroups; g++) {
         Work wg = w0;
@@ -1291,7 +1322,8 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
         if (t <= w.max_iter && !w.layered)
-            err = cudaLaunchKernel(vn_kernel_for(w.fmt), vn_grid(T, F), dim3(kThreads), args, 0, stream);
+            err = cudaLaunchKernel(vn_launch(T, F, w.fmt).func, vn_launch(T, F, w.fmt).grid,
+                                   dim3(kThreads), args, 0, stream);
         for (int g = 0; t <= w.max_iter && w.layered && g < w.ngroups && err == cudaSuccess; g++) {
             Work wg = w;
             wg.pass = kPassGroup;
@@ -1565,7 +1597,8 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
         err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
     cudaEventRecord(ev[1], stream);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel(vn_kernel_for(w.fmt), vn_grid(T, n_frames), dim3(kThreads), args, 0,
+        err = cudaLaunchKernel(vn_launch(T, n_frames, w.fmt).func, vn_launch(T, n_frames, w.fmt).grid,
+                               dim3(kThreads), args, 0,
                                stream);
     cudaEventRecord(ev[2], stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
@@ -1783,7 +1816,8 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
             err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),
                              ctrl_args);
         if (err == cudaSuccess)
-            err = add_kernel(&c, g, &b, 1, vn_kernel_for(pool->w.fmt), vn_grid(T, F), dim3(kThreads),
+            err = add_kernel(&c, g, &b, 1, vn_launch(T, F, pool->w.fmt).func,
+                             vn_launch(T, F, pool->w.fmt).grid, dim3(kThreads),
                              args);
         prev = c;
     }
