@@ -107,3 +107,65 @@ def threshold(B: np.ndarray, lo: float = 1e-3, hi: float = 10.0, rel: float = 1e
 def rate(B: np.ndarray) -> float:
     """Design rate 1 - mb / nb of a full-rank base matrix."""
     return 1.0 - B.shape[0] / B.shape[1]
+
+
+# ------------------------------------------------------- multi-edge ensembles
+
+def met_converges(vn_types, cn_types, snr: float, max_iter: int = 5000,
+                  tol: float = 1e-6) -> bool:
+    """EXIT analysis (Gaussian approximation) of a multi-edge-type ensemble.
+
+    ``vn_types`` / ``cn_types``: lists of (fraction, degree vector d), d[t]
+    sockets of edge type t (all variable nodes see the channel). Tracks one
+    mutual information per edge type and direction; a node type's outgoing
+    information on type t averages over the node types in proportion to
+    their type-t sockets. Converges when every variable type with sockets
+    reaches a-posteriori information 1."""
+    T = len(vn_types[0][1])
+    vw = np.array([w for w, _ in vn_types], dtype=np.float64)
+    vd = np.array([d for _, d in vn_types], dtype=np.float64)
+    cw = np.array([w for w, _ in cn_types], dtype=np.float64)
+    cd = np.array([d for _, d in cn_types], dtype=np.float64)
+    v_edges = (vw[:, None] * vd).sum(axis=0)   # sockets per type, variable side
+    c_edges = (cw[:, None] * cd).sum(axis=0)
+    s_ch2 = 4.0 * snr
+    i_cv = np.zeros(T)                          # check -> variable, per type
+    for _ in range(max_iter):
+        a = J_inv(i_cv) ** 2                    # per type
+        tot = vd @ a + s_ch2                    # per variable type
+        i_vc = np.zeros(T)
+        for t in range(T):
+            if v_edges[t] <= 0:
+                continue
+            out = J_fast(np.sqrt(np.maximum(tot - a[t], 0.0)))
+            i_vc[t] = np.sum(vw * vd[:, t] * out) / v_edges[t]
+        b = J_inv(1.0 - i_vc) ** 2
+        tot_c = cd @ b
+        for t in range(T):
+            if c_edges[t] <= 0:
+                continue
+            out = 1.0 - J_fast(np.sqrt(np.maximum(tot_c - b[t], 0.0)))
+            i_cv[t] = np.sum(cw * cd[:, t] * out) / c_edges[t]
+        app = J_fast(np.sqrt(vd @ (J_inv(i_cv) ** 2) + s_ch2))
+        if np.all(app > 1.0 - tol):
+            return True
+    return False
+
+
+def met_threshold(vn_types, cn_types, lo: float = 1e-3, hi: float = 10.0,
+                  rel: float = 1e-3, max_iter: int = 5000) -> float:
+    """Smallest SNR at which met_converges holds (bisection in log SNR)."""
+    if not met_converges(vn_types, cn_types, hi, max_iter):
+        raise ValueError("does not converge even at the upper SNR bound")
+    while hi / lo > 1.0 + rel:
+        mid = np.sqrt(lo * hi)
+        if met_converges(vn_types, cn_types, mid, max_iter):
+            hi = mid
+        else:
+            lo = mid
+    return float(hi)
+
+
+def met_rate(vn_types, cn_types) -> float:
+    """Omega(1) - Psi(1) of normalised multi-edge degree distributions."""
+    return sum(w for w, _ in vn_types) - sum(w for w, _ in cn_types)

@@ -65,3 +65,34 @@ def test_base_matrix_counts_circulants():
     assert B.shape == (49, 50)
     assert B[:, 0].sum() == 60 and B[:, 1].sum() == 59
     assert np.all(B[np.arange(48), np.arange(2, 50)] == 1)
+
+
+# the paper's rate-0.02 multi-edge ensemble (Sec. III-B); reading c13 swaps the
+# two heavy variable-node fractions so that type-1 sockets balance (41/400)
+PAPER_VN_BALANCED = [(7 / 400, (2, 57, 0)), (9 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
+PAPER_VN_PRINTED = [(9 / 400, (2, 57, 0)), (7 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
+PAPER_CN = [(3 / 320, (3, 0, 0)), (17 / 1600, (7, 0, 0)), (3 / 5, (0, 2, 1)), (9 / 25, (0, 3, 1))]
+PAPER_THRESHOLD = 2.863e-2  # Sec. III-B: density-evolution threshold of the ensemble
+
+
+def test_single_type_met_equals_protograph_exit():
+    assert pexit.met_threshold([(1.0, (3,))], [(0.5, (6,))]) == pytest.approx(
+        pexit.threshold(np.array([[3, 3]])), rel=2e-3)
+
+
+def test_paper_ensemble_sockets_rate_and_threshold():
+    vn, cn = PAPER_VN_BALANCED, PAPER_CN
+    for t in range(3):
+        v = sum(w * d[t] for w, d in vn)
+        c = sum(w * d[t] for w, d in cn)
+        assert v == pytest.approx(c), f"edge type {t + 1}"
+    assert sum(w * d[0] for w, d in PAPER_VN_PRINTED) != pytest.approx(
+        sum(w * d[0] for w, d in cn))  # the printed fractions do not balance
+    assert pexit.met_rate(vn, cn) == pytest.approx(0.02)
+    th = pexit.met_threshold(vn, cn, lo=0.005, hi=1.0)
+    th_printed = pexit.met_threshold(PAPER_VN_PRINTED, cn, lo=0.005, hi=1.0)
+    print(f"paper ensemble: EXIT threshold {th:.5f} (balanced reading), "
+          f"{th_printed:.5f} (as printed), density evolution {PAPER_THRESHOLD}")
+    assert th == pytest.approx(PAPER_THRESHOLD, rel=0.03)
+    assert abs(th - PAPER_THRESHOLD) < abs(th_printed - PAPER_THRESHOLD)
+    assert th > _shannon_snr(0.02)
