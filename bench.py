@@ -51,6 +51,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--frames", type=int, default=16, help="frames per step")
     ap.add_argument("--batches", type=int, default=4, help="distinct batches cycled")
+    ap.add_argument("--code", choices=["rate002", "met"], default="rate002",
+                    help="rate002: the 49x50 seeded protograph (the headline workload); met: a "
+                         "code sampled from the paper's multi-edge distribution (1568x1600, Z=625)")
     ap.add_argument("--Z", type=int, default=20000)
     ap.add_argument("--snr", type=float, default=0.029)
     ap.add_argument("--max-iter", type=int, default=500)
@@ -235,10 +238,11 @@ def ncu_traffic(pass_name: str, msg_format: str, frames: int):
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_sample(Z, snr, iters, seed):
-    """Time the FP64 oracle on one frame: 8-D map plus `iters` iterations."""
+def oracle_sample(Z, snr, iters, seed, d=None):
+    """Time the FP64 oracle on one frame: 8-D map plus `iters` iterations
+    (the rate-0.02 protograph at Z, or the code dict d)."""
     import oracle
-    d = synth.rate002_code(Z)
+    d = synth.rate002_code(Z) if d is None else d
     code = oracle.Code.from_dict(d)
     x, y, bits = synth.channel_frame(code.n, snr, seed)
     m32 = oracle.bob_message(y, bits).astype(np.float32)
@@ -303,7 +307,7 @@ def run_ours(args, world, rank, local):
     q.load()
     stream = torch.cuda.current_stream()
 
-    d = synth.rate002_code(args.Z)
+    d = synth.rate002_code(args.Z) if args.code == "rate002" else synth.met_code(625)
     code = q.create_code_from(d)
     n, k, F, B = code.n, code.k, args.frames, args.batches
     wm, wk = (code.m + 31) // 32, (k + 31) // 32
@@ -447,7 +451,7 @@ def run_ours(args, world, rank, local):
     cn_ms, vn_ms = q.qcldpc_time_passes(code, F, ws, ws_bytes, args.reps, stream)
     col_count = np.bincount(d["col"], minlength=d["nb"])
     heavy = col_count != 1
-    cn_b, vn_b = pass_bytes(args.Z, n_h=int(heavy[d["col"]].sum()),
+    cn_b, vn_b = pass_bytes(d["Z"], n_h=int(heavy[d["col"]].sum()),
                             n_d1=int((~heavy[d["col"]]).sum()), n_hcols=int(heavy.sum()),
                             mb=d["mb"], msg_bytes={"fp32": 4, "fp16": 2, "int8": 1}[args.msg_format])
     peaks, peak_kind = measured_peaks()
@@ -466,7 +470,7 @@ def run_ours(args, world, rank, local):
     cpu = None
     mean_iters = float(np.mean(iters_all))
     if world == 1 and not args.no_cpu_baseline:
-        nn, t_map, t_iter = oracle_sample(args.Z, args.snr, args.cpu_iters, synth.frame_seed(0))
+        nn, t_map, t_iter = oracle_sample(args.Z, args.snr, args.cpu_iters, synth.frame_seed(0), d)
         cpu = {"value": oracle_rate(nn, t_map, t_iter, mean_iters), "unit": UNIT, "cores": 1,
                "kind": "oracle",
                "sample": (f"1 frame (n={nn}): FP64 8-D map + {args.cpu_iters} flooding "
@@ -481,7 +485,9 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "msg_format": args.msg_format,
         "schedule": args.schedule if not layered else f"layered, {args.layers or d['mb']} row groups",
-        "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "k": k, "snr": args.snr,
+        "config": {"workload": WORKLOAD if args.code == "rate002" else
+                   "met_rate0.02_n1e6_snr%g_max%dit_%dframes" % (args.snr, args.max_iter, F),
+                   "code": args.code, "Z": d["Z"], "n": n, "k": k, "snr": args.snr,
                    "frames_per_step": F, "distinct_frames": frames_total,
                    "max_iter": args.max_iter, "stop_test": "after every iteration",
                    "parallelism": f"replicas x{world}",

@@ -109,7 +109,8 @@ def emit(line: dict):
 # --------------------------------------------------------------------- fer
 
 # n = 10^6 member of each rate, for the FER study
-FER_CODES = {"r002": (synth.rate002_code, 20000, "rate 0.02"),
+FER_CODES = {"met": (synth.met_code, 625, "rate 0.02 multi-edge (paper's distribution)"),
+             "r002": (synth.rate002_code, 20000, "rate 0.02"),
              "r005": (synth.rate005_code, 50000, "rate 0.05"),
              "r010": (synth.rate010_code, 100000, "rate 0.10")}
 

@@ -3,7 +3,9 @@
  * in long-distance CV-QKD reverse reconciliation (arXiv 1702.07740).
  *
  * C ABI. Every device buffer is owned by the caller; the library never
- * allocates device memory, never frees or synchronises caller memory, and
+ * allocates device memory at run time (code tables and the no-alloc scratch
+ * are static device arrays of the library), never frees or synchronises
+ * caller memory, and
  * every call that takes a stream only enqueues work on it. Calls return 0 on success or a
  * negative QCLDPC_E_* status; qcldpc_last_error() then describes the failure
  * (thread-local text, valid until the next failing call on the same thread).
@@ -34,17 +36,21 @@ enum {
     QCLDPC_E_SHIFT_RANGE = -2, /* circulant shift outside [0, Z) */
     QCLDPC_E_DUP_SHIFT = -3,   /* two circulants with equal shift in one base entry */
     QCLDPC_E_ALIGN = -4,       /* pointer not aligned as required */
-    QCLDPC_E_NOMEM = -5,       /* host allocation failed or workspace too small */
+    QCLDPC_E_NOMEM = -5,       /* host allocation failed, workspace too small, or
+                                  the device table arena is full */
     QCLDPC_E_CUDA = -6,        /* a CUDA runtime call failed */
     QCLDPC_E_TIMEOUT = -7,     /* reserved: a bounded device wait gave up */
     QCLDPC_E_UNSUPPORTED = -8  /* code exceeds a compile-time table limit */
 };
 
-/* Compile-time table limits of this build (checked by qcldpc_create_code). */
-#define QCLDPC_MAX_BASE_ROWS 128
-#define QCLDPC_MAX_BASE_COLS 512
-#define QCLDPC_MAX_CIRCULANTS 512
-#define QCLDPC_MAX_HEAVY_COLS 32
+/* Table limits of this build (checked by qcldpc_create_code). The tables of
+ * all live codes share a 16 MiB static device arena inside the library (about
+ * 60 bytes per circulant); a code takes its block on the first call that
+ * launches work and returns it in qcldpc_destroy_code. */
+#define QCLDPC_MAX_BASE_ROWS 16384
+#define QCLDPC_MAX_BASE_COLS 32768
+#define QCLDPC_MAX_CIRCULANTS 65536
+#define QCLDPC_MAX_HEAVY_COLS 4096
 #define QCLDPC_MAX_ROW_DEGREE 16
 #define QCLDPC_MAX_Z (1 << 24)
 
@@ -277,7 +283,7 @@ int qcldpc_pool_collect(qcldpc_pool *pool, int n, const int32_t *slots_dev,
 /*
  * Schedule autotuner; an extension (the paper fixes flooding). Decodes the
  * caller's sample batch once per candidate schedule: flooding, then layered
- * with 2, 7 and mb row groups (those in [1, mb], without repeats). Every
+ * with 2, 7 and min(mb, 64) row groups (those in [1, mb], without repeats). Every
  * other option comes from p. Each candidate runs once untimed (its graph is
  * instantiated), then `reps` times between CUDA events on `stream`; the
  * fastest candidate's options are written to *best. What is timed is the
@@ -290,7 +296,7 @@ int qcldpc_pool_collect(qcldpc_pool *pool, int n, const int32_t *slots_dev,
  *   reps                   >= 1 timed decodes per candidate
  *   best                   HOST qcldpc_params, written on success
  *   times_ms               optional HOST float[4]: mean decode time per
- *                          candidate (flooding, 2, 7, mb groups), NAN where
+ *                          candidate (flooding, 2, 7, min(mb, 64) groups), NAN where
  *                          a candidate was not tried
  * Blocks the calling thread until the timings are known. Errors as
  * qcldpc_decode.

@@ -70,6 +70,7 @@
 namespace {
 
 using qc::Table;
+using qc::exact_shape;
 
 // Launch shapes (overridable at build time for tuning sweeps). Defaults
 // from a sweep at Z = 20,000 with 16 frames on GB300.
@@ -82,6 +83,7 @@ using qc::Table;
 constexpr int kThreads = 256;
 constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
 constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
+constexpr int kColChunk = 128;  // heavy-column circulants staged per chunk by the variable pass
 constexpr int kCtrlThreads = 256;
 constexpr int kGraphCacheSize = 8;
 // Check-node pass with bulk-copy staging: one block stages kTile consecutive
@@ -231,6 +233,16 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 constexpr uint32_t kSign = 0x80000000u;
+
+// The off_a / off_b of a row's entries from its descriptor (three 16-byte
+// read-only loads; the first 16 bytes, r / rp / nh / nd, the caller has).
+__device__ __forceinline__ void load_offsets(const qc::RowDesc *dp, int (&oa)[qc::kDescEnts],
+                                             int (&ob)[qc::kDescEnts]) {
+    const int4 *q = reinterpret_cast<const int4 *>(dp);
+    const int4 q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
+    oa[0] = q1.x; oa[1] = q1.y; oa[2] = q1.z; oa[3] = q1.w; oa[4] = q2.x; oa[5] = q2.y;
+    ob[0] = q2.z; ob[1] = q2.w; ob[2] = q3.x; ob[3] = q3.y; ob[4] = q3.z; ob[5] = q3.w;
+}
 __device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
 
 // Storage formats of the check-to-variable messages (computation is FP32):
@@ -495,8 +507,8 @@ __device__ __noinline__ void soft_deg1(const Table &T, const Work &W, int f, int
 }
 
 template <int NH, int ND, int MODE, typename M>
-__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int t,
-                                        unsigned char *smem) {
+__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int rp, int t,
+                                        const qc::RowDesc *dp, unsigned char *smem) {
     constexpr int D = NH + ND;
     constexpr int NHa = NH > 0 ? NH : 1;
     constexpr int NDa = ND > 0 ? ND : 1;
@@ -505,7 +517,8 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
     constexpr int kWordStep = kThreads / 32;
     const int Z = T.Z, ZW = W.ZW;
-    const int rp = T.row_ptr[r];
+    int oa[qc::kDescEnts], ob[qc::kDescEnts];
+    load_offsets(dp, oa, ob);
     const int i0 = blockIdx.x * kTile;
     const int tid = threadIdx.x;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -544,20 +557,20 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
             ncopy++;
         };
 #pragma unroll
-        for (int k = 0; k < NH; k++) add(L + T.row_off_a[rp + k] + i0, kTile, 4, kStage);
+        for (int k = 0; k < NH; k++) add(L + oa[k] + i0, kTile, 4, kStage);
         if (kReadMsg) {
 #pragma unroll
             for (int k = 0; k < NH; k++)
-                add(msg_rd + T.row_off_b[rp + k] + i0, kTile, (int)sizeof(M), kStage);
+                add(msg_rd + ob[k] + i0, kTile, (int)sizeof(M), kStage);
         }
         if (kUpdate) {
 #pragma unroll
-            for (int k = 0; k < ND; k++) add(phiq + T.row_off_a[rp + NH + k] + i0, kTile, 4, kStage);
+            for (int k = 0; k < ND; k++) add(phiq + oa[NH + k] + i0, kTile, 4, kStage);
         }
         if (kTest) {
 #pragma unroll
             for (int k = 0; k < ND; k++)
-                add(bprev + T.row_off_b[rp + NH + k] + (i0 >> 5), kTile / 32, 4, kStageWords);
+                add(bprev + ob[NH + k] + (i0 >> 5), kTile / 32, 4, kStageWords);
         }
         mbar_expect_tx(bar, total);
         for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
@@ -594,8 +607,8 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
         uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
 #pragma unroll
         for (int k = 0; k < D; k++) {
-            if (k < NH) oM[k] = msg + T.row_off_b[rp + k] + i0 + tid;
-            else oB[k - NH] = bcur + T.row_off_b[rp + k] + (i0 >> 5) + (tid >> 5);
+            if (k < NH) oM[k] = msg + ob[k] + i0 + tid;
+            else oB[k - NH] = bcur + ob[k] + (i0 >> 5) + (tid >> 5);
         }
     }
     const int c0 = r * Z + i0 + tid;
@@ -764,22 +777,20 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
 
 template <int MODE, typename M>
 __device__ __forceinline__ bool cn_tile_dispatch(const Table &T, const Work &W, int f, int r, int t,
-                                                 int nh, int nd, unsigned char *smem) {
+                                                 int rp, int nh, int nd, const qc::RowDesc *dp,
+                                                 unsigned char *smem) {
     switch (nh * 4 + nd) {
-        case 1 * 4 + 1: return cn_tile<1, 1, MODE, M>(T, W, f, r, t, smem);
-        case 2 * 4 + 0: return cn_tile<2, 0, MODE, M>(T, W, f, r, t, smem);
-        case 2 * 4 + 1: return cn_tile<2, 1, MODE, M>(T, W, f, r, t, smem);
-        case 3 * 4 + 0: return cn_tile<3, 0, MODE, M>(T, W, f, r, t, smem);
-        case 3 * 4 + 1: return cn_tile<3, 1, MODE, M>(T, W, f, r, t, smem);
-        case 4 * 4 + 0: return cn_tile<4, 0, MODE, M>(T, W, f, r, t, smem);
-        case 4 * 4 + 1: return cn_tile<4, 1, MODE, M>(T, W, f, r, t, smem);
+        case 1 * 4 + 1: return cn_tile<1, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 2 * 4 + 0: return cn_tile<2, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 2 * 4 + 1: return cn_tile<2, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 3 * 4 + 0: return cn_tile<3, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 3 * 4 + 1: return cn_tile<3, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 4 * 4 + 0: return cn_tile<4, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
+        case 4 * 4 + 1: return cn_tile<4, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
         default: return false;
     }
 }
 
-__host__ __device__ constexpr bool exact_shape(int nh, int nd) {
-    return (nd == 1 && nh >= 1 && nh <= 4) || (nd == 0 && nh >= 2 && nh <= 4);
-}
 
 // Check-node pass of iteration t, staged variant: grid (ceil(Z / kTile), base
 // row, frame), dynamic shared memory sized by cn_tma_smem for the code's
@@ -792,7 +803,9 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kern
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
     const bool group = W.pass == kPassGroup;
-    const int r = group ? W.lrow0 + (int)blockIdx.y : T.row_order[blockIdx.y];
+    const qc::RowDesc *dp = group ? T.row_desc + (W.lrow0 + (int)blockIdx.y) : T.row_desc_ord + blockIdx.y;
+    const int4 head = __ldg(reinterpret_cast<const int4 *>(dp));  // r, rp, nh, nd
+    const int r = head.x;
     const int t = W.t[f] - (group ? 1 : 0);
     int mode = t > W.max_iter ? kTestOnly
                : t == 1       ? kFirst
@@ -804,15 +817,14 @@ __global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kern
         if (mode == kTestOnly) return;
         if (mode == kSteadyTest) mode = kSteady;
     }
-    const int nh = T.row_nh[r];
-    const int nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
+    const int rp = head.y, nh = head.z, nd = head.w;
     bool bad;
     if (exact_shape(nh, nd)) {
         switch (mode) {
-            case kFirst: bad = cn_tile_dispatch<kFirst, M>(T, W, f, r, t, nh, nd, smem); break;
-            case kSteady: bad = cn_tile_dispatch<kSteady, M>(T, W, f, r, t, nh, nd, smem); break;
-            case kSteadyTest: bad = cn_tile_dispatch<kSteadyTest, M>(T, W, f, r, t, nh, nd, smem); break;
-            default: bad = cn_tile_dispatch<kTestOnly, M>(T, W, f, r, t, nh, nd, smem); break;
+            case kFirst: bad = cn_tile_dispatch<kFirst, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
+            case kSteady: bad = cn_tile_dispatch<kSteady, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
+            case kSteadyTest: bad = cn_tile_dispatch<kSteadyTest, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
+            default: bad = cn_tile_dispatch<kTestOnly, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
         }
     } else {
         bad = cn_row_generic<MAXD, M>(T, W, f, r, t, mode, blockIdx.x * kTile + threadIdx.x, kTmaVpt);
@@ -875,7 +887,8 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 // read only in range.
 template <typename M, int VPT>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
-                                                      const __grid_constant__ Work W) {
+                                                      const __grid_constant__ Work W,
+                                                      const __grid_constant__ qc::ColsInline C) {
     pdl_wait();  // the control step's flags are complete and visible
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;
@@ -891,17 +904,42 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
         const int j = j0 + u * kThreads;
         acc[u] = j < Z ? __ldg(q + j) * kLog2e : 0.0f;
     }
-    const int ce = T.col_ptr[hc + 1];
+    if (C.ok) {
+        // the column's circulants from the inline copy (constant bank)
+        const int ce = C.col_ptr[hc + 1];
 #pragma unroll kVnUnroll
-    for (int k = T.col_ptr[hc]; k < ce; k++) {
-        const qc::ColEnt e = T.cols[k];
-        const M *__restrict__ mk = msg + e.id * Z;
+        for (int k = C.col_ptr[hc]; k < ce; k++) {
+            const qc::ColEnt e = C.cols[k];
+            const M *__restrict__ mk = msg + e.id * Z;
 #pragma unroll
-        for (int u = 0; u < VPT; u++) {
-            int idx = j0 + u * kThreads - e.shift;
-            if (idx < 0) idx += Z;
-            acc[u] += Codec<M>::dec(mk[idx], W);
+            for (int u = 0; u < VPT; u++) {
+                int idx = j0 + u * kThreads - e.shift;
+                if (idx < 0) idx += Z;
+                acc[u] += Codec<M>::dec(mk[idx], W);
+            }
         }
+    } else {
+    // the column's circulants (shift, id), staged in shared memory in chunks
+    __shared__ int2 s_cols[kColChunk];
+    const int cb = T.col_ptr[hc], ce = T.col_ptr[hc + 1];
+    for (int base = cb; base < ce; base += kColChunk) {
+        const int cnt = min(kColChunk, ce - base);
+        __syncthreads();  // the previous chunk is consumed
+        if ((int)threadIdx.x < cnt)
+            s_cols[threadIdx.x] = __ldg(reinterpret_cast<const int2 *>(T.cols) + base + threadIdx.x);
+        __syncthreads();
+#pragma unroll kVnUnroll
+        for (int kk = 0; kk < cnt; kk++) {
+            const int2 e = s_cols[kk];  // (shift, id)
+            const M *__restrict__ mk = msg + e.y * Z;
+#pragma unroll
+            for (int u = 0; u < VPT; u++) {
+                int idx = j0 + u * kThreads - e.x;
+                if (idx < 0) idx += Z;
+                acc[u] += Codec<M>::dec(mk[idx], W);
+            }
+        }
+    }
     }
 #pragma unroll
     for (int u = 0; u < VPT; u++) {
@@ -1149,13 +1187,9 @@ struct CnLaunch {
 CnLaunch cn_launch(const Table &T, int F, int fmt) {
     CnLaunch c;
     {
-        size_t smem = kSmemHeader;
-        for (int r = 0; r < T.mb; r++) {
-            const int nh = T.row_nh[r], nd = T.row_ptr[r + 1] - T.row_ptr[r] - nh;
-            if (!exact_shape(nh, nd)) continue;
-            const size_t b = kSmemHeader + (size_t)(2 * nh + nd) * kStage * 4 + (size_t)nd * kStageWords * 4;
-            smem = std::max(smem, b);
-        }
+        // the code's widest exact-shape row (its staged rows and word rows)
+        const size_t smem = kSmemHeader + (size_t)T.stage_rows_max * kStage * 4 +
+                            (size_t)T.stage_words_max * kStageWords * 4;
         c.func = cn_tma_kernel_for(T.max_row_deg, fmt);
         c.grid = dim3((unsigned)((T.Z + kTile - 1) / kTile), (unsigned)T.mb, (unsigned)F);
         c.smem = smem;
@@ -1222,12 +1256,14 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
 // Loop body of the decode graph. Flooding: check pass -> control ->
 // variable pass. Layered: stop-test pass -> control -> for every row group,
 // its check pass -> its posterior update.
-cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
-                          cudaGraphConditionalHandle handle) {
+cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline &CI,
+                          const Work &w0, cudaGraphConditionalHandle handle) {
     const int F = w0.n_frames;
     Table tcopy = T;
     Work wcopy = w0;
+    qc::ColsInline ccopy = CI;
     void *args[] = {&tcopy, &wcopy};
+    void *vn_args[] = {&tcopy, &wcopy, &ccopy};
     cudaGraphNode_t n_cn, n_ctrl, n_vn;
     const CnLaunch cl = cn_launch(T, F, w0.fmt);
     cudaError_t err;
@@ -1242,7 +1278,8 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const Work &w0,
         return err;
     if (!w0.layered) {
         const VnLaunch vl = vn_launch(T, F, w0.fmt);
-        return add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), args, 0, true);
+        return add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0,
+                          true);
     }
     cudaGraphNode_t prev = n_ctrl;
     for (int g = 0; g < w0.ngroups; g++) {
@@ -1291,7 +1328,7 @@ int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
     if ((err = cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add conditional node");
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    if ((err = add_loop_body(body, T, w0, handle)) != cudaSuccess)
+    if ((err = add_loop_body(body, T, code->cols_in, w0, handle)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add loop body");
     if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks),
                           dim3(kThreads), args)) != cudaSuccess)
@@ -1321,9 +1358,12 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
-        if (t <= w.max_iter && !w.layered)
-            err = cudaLaunchKernel(vn_launch(T, F, w.fmt).func, vn_launch(T, F, w.fmt).grid,
-                                   dim3(kThreads), args, 0, stream);
+        if (t <= w.max_iter && !w.layered) {
+            qc::ColsInline ccopy = code->cols_in;
+            void *vn_args[] = {&tcopy, &wcopy, &ccopy};
+            const VnLaunch vl = vn_launch(T, F, w.fmt);
+            err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
+        }
         for (int g = 0; t <= w.max_iter && w.layered && g < w.ngroups && err == cudaSuccess; g++) {
             Work wg = w;
             wg.pass = kPassGroup;
@@ -1380,6 +1420,7 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (err != cudaSuccess) return cuda_fail(err, "decode: cudaGetDevice");
     if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode: current device differs from the code's device");
 
+    if (int st = upload_tables(code)) return st;
     const Table &T = code->tab;
     const bool layered = p.schedule == 1;
     const Layout lo = layout_of(T, F, soft, p.msg_format, layered);
@@ -1516,7 +1557,9 @@ extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,
     if (p_in) base = *p_in;
     else qcldpc_params_init(&base);
     const int mb = code->tab.mb;
-    const int want[4] = {0, 2, 7, mb};  // 0: flooding, else layered with that many groups
+    // 0: flooding, else layered with that many row groups (at most 64: a
+    // group costs two launches per iteration)
+    const int want[4] = {0, 2, 7, std::min(mb, 64)};
     if (times_ms)
         for (int i = 0; i < 4; i++) times_ms[i] = NAN;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1529,7 +1572,7 @@ extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,
     float best_ms = INFINITY;
     int st = QCLDPC_OK;
     for (int i = 0; i < 4 && st == QCLDPC_OK; i++) {
-        if (i > 0 && (want[i] > mb || (i == 3 && (mb == 2 || mb == 7)))) continue;
+        if (i > 0 && (want[i] > mb || (i == 3 && (want[3] == 2 || want[3] == 7)))) continue;
         qcldpc_params p = base;
         p.schedule = want[i] ? 1 : 0;
         p.layers = want[i];
@@ -1596,10 +1639,11 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     for (int r = 0; r < reps && err == cudaSuccess; r++)
         err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
     cudaEventRecord(ev[1], stream);
+    qc::ColsInline ccopy = code->cols_in;
+    void *vn_args[] = {&tcopy, &w, &ccopy};
+    const VnLaunch vl = vn_launch(T, n_frames, w.fmt);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel(vn_launch(T, n_frames, w.fmt).func, vn_launch(T, n_frames, w.fmt).grid,
-                               dim3(kThreads), args, 0,
-                               stream);
+        err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
     cudaEventRecord(ev[2], stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -1802,10 +1846,13 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
     const int F = pool->n_slots;
     Table tcopy = T;
     Work wcopy = pool->w;
+    qc::ColsInline ccopy = pool->code->cols_in;
     void *args[] = {&tcopy, &wcopy};
+    void *vn_args[] = {&tcopy, &wcopy, &ccopy};
     cudaGraphConditionalHandle none = 0;
     void *ctrl_args[] = {&wcopy, &none};
     const CnLaunch cl = cn_launch(T, F, pool->w.fmt);
+    const VnLaunch vl = vn_launch(T, F, pool->w.fmt);
     cudaGraphNode_t prev = nullptr;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < n_passes && err == cudaSuccess; i++) {
@@ -1816,9 +1863,7 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
             err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),
                              ctrl_args);
         if (err == cudaSuccess)
-            err = add_kernel(&c, g, &b, 1, vn_launch(T, F, pool->w.fmt).func,
-                             vn_launch(T, F, pool->w.fmt).grid, dim3(kThreads),
-                             args);
+            err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
         prev = c;
     }
     *last = prev;
@@ -1864,6 +1909,7 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
         !(p.msg_step >= 0.0f) || p.soft_output)
         return fail(QCLDPC_E_INVAL, "pool_create: unsupported option");
     if (!aligned(workspace_dev, 256)) return fail(QCLDPC_E_ALIGN, "pool_create: workspace must be 256-byte aligned");
+    if (int st = upload_tables(code)) return st;
     const Layout2 lo = pool_layout(code, n_slots, p.msg_format);
     if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "pool_create: workspace too small");
     int dev = -1;

@@ -188,6 +188,7 @@ extern "C" int qcldpc_syndrome(const qcldpc_code *code, const uint32_t *bits_dev
         return fail(QCLDPC_E_ALIGN, "syndrome: buffers must be 4-byte aligned");
     if (n_frames > 65535) return fail(QCLDPC_E_INVAL, "syndrome: more than 65535 frames");
     if (n_frames == 0) return QCLDPC_OK;
+    if (int st = upload_tables(const_cast<qcldpc_code *>(code))) return st;
     const int64_t words_n = (code->n + 31) / 32, words_m = (code->m + 31) / 32;
     dim3 grid((unsigned)((code->m + 255) / 256), (unsigned)n_frames);
     syndrome_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(code->tab, bits_dev, syn_dev,

@@ -296,7 +296,8 @@ def qcldpc_time_passes(code: Code, n_frames: int, workspace_dev, workspace_bytes
     return cn.value, vn.value
 
 
-AUTOTUNE_CANDIDATES = ("flooding", "layered 2 groups", "layered 7 groups", "layered mb groups")
+AUTOTUNE_CANDIDATES = ("flooding", "layered 2 groups", "layered 7 groups",
+                       "layered min(mb,64) groups")
 
 
 def qcldpc_autotune(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,

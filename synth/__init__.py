@@ -13,6 +13,8 @@ Workload recipe (stand-in for the paper's codes, which are not published):
   gives every row that many circulants instead). The remaining columns are
   degree-1 identity blocks on rows 0, 1, ... (shift 0), forming the long
   unshifted diagonal of Sec. III-D. Shifts are uniform in [0, Z).
+* ``met_code``: a QC code sampled from the paper's rate-0.02 multi-edge
+  degree distribution (Sec. III-B), 1600 base columns, 1568 base rows.
 * ``channel_frame``: x ~ N(0,1), z ~ N(0, 1/snr), y = x + z (the virtual
   BIAWGN channel of Sec. II-C) and Bob's uniform bits.
 
@@ -64,6 +66,74 @@ def protograph_code(mb: int = 49, Z: int = 512, n_heavy: int = 2,
         "col": arr[:, 1].astype(np.int32),
         "shift": arr[:, 2].astype(np.int32),
     }
+
+
+# The paper's rate-0.02 multi-edge distribution (Sec. III-B) in integral form
+# on 1600 base columns, the smallest size at which every fraction is whole,
+# with the heavy variable-node fractions read as 7/400 and 9/400 so that the
+# type-1 sockets balance (41/400 on both sides).
+MET_VN = ((28, 2, 57), (36, 3, 57))          # (count, type-1 degree, type-2 degree)
+MET_DEG1_VN = 1536                           # x3 (degree-1, type 3)
+MET_CN_T1 = ((15, 3), (17, 7))               # (count, type-1 degree)
+MET_CN_T2 = ((960, 2), (576, 3))             # (count, type-2 degree), each with one x3
+
+
+def met_code(Z: int, seed: int = CODE_SEED) -> dict:
+    """Circulant list of a QC code sampled from the paper's rate-0.02
+    multi-edge degree distribution.
+
+    Base columns 0..63 are the heavy variable nodes (28 with 2 type-1 and 57
+    type-2 sockets, then 36 with 3 and 57), columns 64..1599 the degree-1
+    nodes. Base rows 0..1535 are the type-2 checks (960 with 2 type-2
+    sockets, then 576 with 3), each with its own degree-1 column (row r,
+    column 64 + r, shift 0); rows 1536..1567 the type-1 checks (15 of degree
+    3, then 17 of degree 7). Within each edge type the sockets are matched by
+    a seeded random permutation; sockets that land in the same base entry
+    become circulants with distinct shifts. Shifts are uniform in [0, Z).
+    The key bits (k = 32 Z) are heavy columns 0..31.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_heavy = sum(c for c, _, _ in MET_VN)
+    n_t2 = sum(c for c, _ in MET_CN_T2)
+    n_t1 = sum(c for c, _ in MET_CN_T1)
+    mb, nb = n_t2 + n_t1, n_heavy + MET_DEG1_VN
+    assert MET_DEG1_VN == n_t2
+    # variable-side sockets per edge type (column per socket)
+    v1, v2, col = [], [], 0
+    for count, d1, d2 in MET_VN:
+        for _ in range(count):
+            v1 += [col] * d1
+            v2 += [col] * d2
+            col += 1
+    c2, row = [], 0
+    for count, d2 in MET_CN_T2:
+        for _ in range(count):
+            c2 += [row] * d2
+            row += 1
+    c1 = []
+    for count, d1 in MET_CN_T1:
+        for _ in range(count):
+            c1 += [row] * d1
+            row += 1
+    assert len(v1) == len(c1) and len(v2) == len(c2)
+    pairs = list(zip(c1, rng.permutation(v1))) + list(zip(c2, rng.permutation(v2)))
+    # group sockets by base entry, draw distinct shifts per entry
+    entries = {}
+    for r, c in pairs:
+        entries[(int(r), int(c))] = entries.get((int(r), int(c)), 0) + 1
+    out = []
+    for (r, c), k in sorted(entries.items()):
+        if k > Z:
+            raise ValueError("more circulants in one base entry than shifts")
+        for s in rng.choice(Z, size=k, replace=False):
+            out.append((r, c, int(s)))
+    for d in range(MET_DEG1_VN):
+        out.append((d, n_heavy + d, 0))
+    out.sort(key=lambda e: (e[0], e[1]))
+    arr = np.array(out, dtype=np.int64).reshape(-1, 3)
+    return {"mb": mb, "nb": nb, "Z": Z,
+            "row": arr[:, 0].astype(np.int32), "col": arr[:, 1].astype(np.int32),
+            "shift": arr[:, 2].astype(np.int32)}
 
 
 def rate002_code(Z: int, seed: int = CODE_SEED) -> dict:

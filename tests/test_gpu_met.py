@@ -1,0 +1,69 @@
+"""The decoder on codes sampled from the paper's multi-edge distribution
+(1568 x 1600 base matrices: tables in the device table arena, type-1 rows of
+degree 7 on the generic check-node path) against the FP64 oracle. Bars as in
+test_gpu_parity."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from frames import make_frames
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1702_07740_gb300 import qcldpc as q  # noqa: E402
+from test_gpu_parity import assert_posteriors_close, decode_soft, gpu_llr  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device visible")
+    q.load()
+
+
+@pytest.mark.parametrize("Z, F", [(3, 2), (16, 3)])
+def test_met_code_fixed_iterations_match_oracle(Z, F):
+    fr = make_frames(synth.met_code(Z), 0.05, F)
+    code = q.create_code_from(fr.code_dict)
+    iters = 25
+    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, F, iters, et_start=iters + 1)
+    for f in range(F):
+        ref, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], iters, et_start=iters + 1)
+        err = assert_posteriors_close(post[f], ref, f"Z={Z} frame {f}")
+        assert its[f] == it and conv[f] == int(cv)
+        print(f"MET Z={Z} frame {f}: max scaled err {err.max():.2e}")
+
+
+def test_met_code_early_stop_matches_oracle():
+    fr = make_frames(synth.met_code(16), 0.2, 4)
+    code = q.create_code_from(fr.code_dict)
+    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, fr.F, 100)
+    n_conv = 0
+    for f in range(fr.F):
+        ref, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], 100)
+        assert (its[f], conv[f]) == (it, int(cv)), f"frame {f}"
+        if cv:
+            n_conv += 1
+            np.testing.assert_array_equal(keys[f], chat[: fr.code.k])
+    assert n_conv > 0
+
+
+def test_met_code_full_size_few_iterations():
+    """n = 10^6 (Z = 625), 4 frames; frame 0 against the oracle after 3 iterations."""
+    d = synth.met_code(625)
+    fr = make_frames(d, 0.03, 1)
+    code = q.create_code_from(d)
+    F = 4
+    x = np.concatenate([fr.x32] * F)
+    m = np.concatenate([fr.m32] * F)
+    syn = np.concatenate([fr.syn] * F)
+    n = fr.code.n
+    llr = torch.empty(F * n, dtype=torch.float32, device="cuda")
+    q.qcldpc_llr_8d(torch.from_numpy(x.reshape(-1)).cuda(), torch.from_numpy(m.reshape(-1)).cuda(),
+                    F * n, 0.03, llr)
+    _, _, _, post = decode_soft(code, llr, syn, F, 3, et_start=4)
+    ref, _, _, _ = oracle.decode(fr.code, fr.q64[0], fr.syn[0], 3, et_start=4)
+    for f in range(F):
+        assert_posteriors_close(post[f], ref, f"frame {f}")
