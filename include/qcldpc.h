@@ -44,8 +44,9 @@ enum {
 };
 
 /* Table limits of this build (checked by qcldpc_create_code). The tables of
- * all live codes share a 16 MiB static device arena inside the library (about
- * 60 bytes per circulant); a code takes its block on the first call that
+ * all live codes share a 64 MiB static device arena inside the library (about
+ * 60 bytes per circulant plus 128 bytes per base row: 0.4 MB for a
+ * 1568 x 1600 base matrix); a code takes its block on the first call that
  * launches work and returns it in qcldpc_destroy_code. */
 #define QCLDPC_MAX_BASE_ROWS 16384
 #define QCLDPC_MAX_BASE_COLS 32768

@@ -43,7 +43,7 @@ void clear_error() { g_last_error.clear(); }
 
 namespace {
 
-constexpr size_t kArenaBytes = size_t(16) << 20;
+constexpr size_t kArenaBytes = size_t(64) << 20;
 __device__ __align__(256) unsigned char g_table_arena[kArenaBytes];
 
 std::mutex g_arena_mu;
@@ -96,7 +96,7 @@ int upload_tables(qcldpc_code *code) {
                          bytes_of(H.d1_row) + bytes_of(H.d1_col);
     size_t off;
     if (!arena_take(total, &off))
-        return fail(QCLDPC_E_NOMEM, "code tables: the device table arena (16 MiB) is full");
+        return fail(QCLDPC_E_NOMEM, "code tables: the device table arena (64 MiB) is full");
     unsigned char *base = nullptr;
     cudaError_t err = cudaGetSymbolAddress(reinterpret_cast<void **>(&base), g_table_arena);
     if (err != cudaSuccess) {

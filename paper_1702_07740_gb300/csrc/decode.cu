@@ -1870,17 +1870,19 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
     return err;
 }
 
-// Graphs stepping several pools at once, cached by (pools, passes).
+// Graphs stepping several pools at once, cached by (pools, passes) with
+// least-recently-used eviction (a server steps changing subsets of its pools).
 struct MultiGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<qcldpc_pool *> pools;
     int passes = 0;
+    unsigned long long stamp = 0;
 };
-constexpr int kMultiGraphs = 8;
+constexpr int kMultiGraphs = 32;
 std::mutex g_multi_mu;
 MultiGraph g_multi[kMultiGraphs];
-int g_multi_next = 0;
+unsigned long long g_multi_clock = 0;
 
 }  // namespace
 
@@ -2045,14 +2047,15 @@ extern "C" int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_p
         return QCLDPC_OK;
     }
     std::lock_guard<std::mutex> lock(g_multi_mu);
-    MultiGraph *hit = nullptr;
-    for (auto &m : g_multi)
+    MultiGraph *hit = nullptr, *victim = &g_multi[0];
+    for (auto &m : g_multi) {
         if (m.exec && m.passes == n_passes && m.pools.size() == (size_t)n_pools &&
             std::equal(m.pools.begin(), m.pools.end(), pools))
             hit = &m;
+        if (!m.exec || (victim->exec && m.stamp < victim->stamp)) victim = &m;
+    }
     if (!hit) {
-        hit = &g_multi[g_multi_next];
-        g_multi_next = (g_multi_next + 1) % kMultiGraphs;
+        hit = victim;
         if (hit->exec) cudaGraphExecDestroy(hit->exec);
         if (hit->graph) cudaGraphDestroy(hit->graph);
         hit->exec = nullptr;
@@ -2072,6 +2075,7 @@ extern "C" int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_p
         hit->pools.assign(pools, pools + n_pools);
         hit->passes = n_passes;
     }
+    hit->stamp = ++g_multi_clock;
     if ((err = cudaGraphLaunch(hit->exec, (cudaStream_t)stream)) != cudaSuccess)
         return cuda_fail(err, "pools_step: cudaGraphLaunch");
     return QCLDPC_OK;

@@ -67,3 +67,31 @@ def test_met_code_full_size_few_iterations():
     ref, _, _, _ = oracle.decode(fr.code, fr.q64[0], fr.syn[0], 3, et_start=4)
     for f in range(F):
         assert_posteriors_close(post[f], ref, f"frame {f}")
+
+
+def test_table_arena_fills_with_nomem_and_frees_on_destroy():
+    """Code tables share a 64 MiB device arena: codes take their block on the
+    first launching call and give it back when destroyed."""
+    d = synth.met_code(2)
+    bits = torch.zeros(1600 * 2 // 32, dtype=torch.int32, device="cuda")
+    syn = torch.zeros((1568 * 2 + 31) // 32, dtype=torch.int32, device="cuda")
+    codes, failed = [], None
+    for i in range(400):  # ~0.4 MB each: the 64 MiB arena holds about 160
+        c = q.create_code_from(d)
+        try:
+            q.qcldpc_syndrome(c, bits, syn, 1)
+        except q.QcldpcError as e:
+            failed = e
+            break
+        codes.append(c)
+    assert failed is not None and "NOMEM" in str(failed)
+    assert 20 <= len(codes) < 400  # other live codes of the session hold blocks too
+    # give back two blocks: the next code fits again
+    del codes[:2]
+    import gc
+    gc.collect()
+    c = q.create_code_from(d)
+    q.qcldpc_syndrome(c, bits, syn, 1)
+    torch.cuda.synchronize()
+    del codes, c
+    gc.collect()
