@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libqcldpc.so")
-SOURCES = ["api.cu", "map.cu", "decode.cu"]
+SOURCES = ["api.cu", "map.cu", "decode.cu", "check_pass_f32.cu", "check_pass_f16.cu", "check_pass_i8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

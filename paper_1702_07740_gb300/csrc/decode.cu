@@ -67,208 +67,9 @@
 
 #include "qcldpc_internal.cuh"
 
+#include "decode_common.cuh"
+
 namespace {
-
-using qc::Table;
-using qc::exact_shape;
-
-// Launch shapes (overridable at build time for tuning sweeps). Defaults
-// from a sweep at Z = 20,000 with 16 frames on GB300.
-#ifndef QCLDPC_VN_VPT
-#define QCLDPC_VN_VPT 3
-#endif
-#ifndef QCLDPC_VN_UNROLL
-#define QCLDPC_VN_UNROLL 6
-#endif
-constexpr int kThreads = 256;
-constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
-constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
-constexpr int kColChunk = 128;  // heavy-column circulants staged per chunk by the variable pass
-constexpr int kCtrlThreads = 256;
-constexpr int kGraphCacheSize = 8;
-// Check-node pass with bulk-copy staging: one block stages kTile consecutive
-// checks of one base row (kTmaVpt per thread) into shared memory.
-#ifndef QCLDPC_CN_TVPT
-#define QCLDPC_CN_TVPT 4
-#endif
-constexpr int kTmaVpt = QCLDPC_CN_TVPT;
-// Resident blocks per SM the staged pass is compiled for (caps registers).
-#ifndef QCLDPC_CN_TMA_MINBLOCKS
-#define QCLDPC_CN_TMA_MINBLOCKS 5
-#endif
-// Programmatic dependent launch inside a flooding iteration: the control and
-// variable passes are scheduled while their predecessor drains and wait for
-// it on the device (griddepcontrol), hiding the launch gaps.
-#ifndef QCLDPC_PDL
-#define QCLDPC_PDL 1
-#endif
-// Evaluate a thread's checks two at a time in packed FP32x2 arithmetic.
-#ifndef QCLDPC_CN_PAIR
-#define QCLDPC_CN_PAIR 1
-#endif
-#ifndef QCLDPC_CN_UNROLL
-#define QCLDPC_CN_UNROLL 4
-#endif
-constexpr int kCnUnroll = QCLDPC_CN_UNROLL;
-constexpr int kTile = kThreads * kTmaVpt;      // checks per block
-constexpr int kStage = kTile + 4;              // staged floats per row (16-byte realignment)
-constexpr int kStageWords = kTile / 32 + 4;    // staged decision words per row
-constexpr int kSmemHeader = 128;               // mbarrier, then 16-byte aligned rows
-constexpr unsigned kWaitLimit = 1u << 22;      // bounded mbarrier polls before giving up
-// Padding elements after every workspace array: lanes and staged copies that
-// run past a row's end read here (results unused), and never past the array.
-constexpr int kSlack = 4096;
-
-// Per-call arguments and workspace pointers (by value in every kernel).
-struct Work {
-    const float *llr;      // [F][n]
-    const uint32_t *syn;   // [F][words_m]
-    uint32_t *keys;        // [F][words_k]
-    int32_t *conv;         // [F]
-    int32_t *iters;        // [F]
-    float *post;           // [F][n] or nullptr
-    int32_t *t;            // [F] iteration each frame is at
-    int32_t *state;        // [F] slot state for pools (0 free, 1 running, 2 stopped) or null
-    int32_t *active;       // [F]
-    int32_t *fail;         // [F] stop-test failures of the current pass
-    int32_t *err;          // device error word (a bounded wait gave up)
-    void *msg;             // [F][n_h][Z] messages in the storage format fmt (layered:
-                           // two such buffers msg_buf elements apart, by iteration parity)
-    float *L;              // [F][n_hcols][2Z]
-    float *phiq;           // [F][n_d1][Z]
-    uint32_t *bits;        // [2][F][n_d1][ZW]
-    float *post1;          // [2][F][n_d1][Z] (soft output only)
-    int64_t n, words_m, words_k;
-    int32_t n_frames, max_iter, et_start, soft, ZW, fmt;
-    float clip, xmin;      // base-2 units
-    float qstep, qinv;     // int8 message quantum and its inverse (base-2 units)
-    int64_t msg_buf;       // layered: elements per message buffer; 0 for flooding
-    int32_t layered;       // schedule: 0 flooding, 1 layered
-    int32_t ngroups;       // layered: row groups per iteration
-    int32_t pass;          // check-pass kind (kPassFlood, kPassTest, kPassGroup)
-    int32_t lrow0, lrows;  // kPassGroup and the group's posterior update: its base rows
-};
-// Kinds of check pass. kPassFlood: flooding iteration t (stop test of t-1
-// when due, then the update). kPassTest: the stop test of iteration t-1
-// alone, when due (layered). kPassGroup: the update of one row group for the
-// iteration the control step just counted on (layered, no test).
-enum CnPass { kPassFlood = 0, kPassTest = 1, kPassGroup = 2 };
-static_assert(sizeof(Work) <= sizeof(((qcldpc_code *)nullptr)->last_work), "Work too large");
-
-// ---------------------------------------------------------------- Phi
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float lg2_approx(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Polynomial pieces derived by paper_1702_07740_gb300/phi_fit.py.
-constexpr float kC = 1.528766394e+00f;  // 1 - log2(ln 2)
-constexpr float kG0 = 5.776225403e-02f;
-constexpr float kG1 = -1.618719543e-03f;
-constexpr float kG2 = 5.430740566e-05f;
-constexpr float kG3 = -1.724728236e-06f;
-constexpr float kA0 = 2.885390043e+00f;
-constexpr float kA1 = 9.617848396e-01f;
-constexpr float kA2 = 5.777652860e-01f;
-constexpr float kA3 = 3.984466195e-01f;
-constexpr float kA4 = 4.293859601e-01f;
-constexpr float kLn2 = 0.6931471805599453f;
-constexpr float kLog2e = 1.4426950408889634f;
-
-// psi(y) = log2 coth(y ln2 / 2) = log2(e) Phi(y ln 2), for y > 0 (callers
-// floor y); Phi(x) = -ln tanh(x/2) is Algorithm 1's check-node function.
-//   small y: psi = 1 - log2(ln 2) - log2(y) + w G(w), w = y^2;
-//   large y: psi = (2/ln 2) atanh(t) = t A(t^2), t = 2^-y.
-// Both pieces are evaluated (no divergence) and combined with a max: each
-// piece underestimates psi outside its own range (split at y = 1/ln 2), so
-// the max picks the accurate piece; they differ only near the split, where
-// both are accurate. Max relative error 2e-7 for y in [1e-6, 60] (ex2/lg2
-// approximations included).
-__device__ __forceinline__ float psi_f(float y) {
-    const float w = y * y;
-    const float g = fmaf(fmaf(fmaf(kG3, w, kG2), w, kG1), w, kG0);
-    const float small = fmaf(w, g, kC - lg2_approx(y));
-    const float t = ex2_approx(-y);
-    const float v = t * t;
-    const float a = fmaf(fmaf(fmaf(fmaf(kA4, v, kA3), v, kA2), v, kA1), v, kA0);
-    return fmaxf(small, t * a);
-}
-
-// psi_f on two arguments at once with the packed FP32x2 multiply-adds of
-// sm_100-class GPUs. Every packed operation rounds each lane exactly as the
-// scalar fmaf / multiply of psi_f does, so psi2(y).x == psi_f(y.x) bit for
-// bit (kC - lg2 is formed as fma(lg2, -1, kC), the same single rounding).
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 psi2(float2 y) {
-    const float2 w = __fmul2_rn(y, y);
-    float2 g = __ffma2_rn(f2(kG3), w, f2(kG2));
-    g = __ffma2_rn(g, w, f2(kG1));
-    g = __ffma2_rn(g, w, f2(kG0));
-    const float2 lc = __ffma2_rn(make_float2(lg2_approx(y.x), lg2_approx(y.y)), f2(-1.0f), f2(kC));
-    const float2 small = __ffma2_rn(w, g, lc);
-    const float2 t = make_float2(ex2_approx(-y.x), ex2_approx(-y.y));
-    const float2 v = __fmul2_rn(t, t);
-    float2 a = __ffma2_rn(f2(kA4), v, f2(kA3));
-    a = __ffma2_rn(a, v, f2(kA2));
-    a = __ffma2_rn(a, v, f2(kA1));
-    a = __ffma2_rn(a, v, f2(kA0));
-    const float2 ta = __fmul2_rn(t, a);
-    return make_float2(fmaxf(small.x, ta.x), fmaxf(small.y, ta.y));
-}
-
-// Programmatic dependent launch: let the next kernel of the graph be
-// scheduled now / wait until the previous kernel's results are visible.
-// Without a programmatic edge both are no-ops.
-__device__ __forceinline__ void pdl_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-constexpr uint32_t kSign = 0x80000000u;
-
-// The off_a / off_b of a row's entries from its descriptor (three 16-byte
-// read-only loads; the first 16 bytes, r / rp / nh / nd, the caller has).
-__device__ __forceinline__ void load_offsets(const qc::RowDesc *dp, int (&oa)[qc::kDescEnts],
-                                             int (&ob)[qc::kDescEnts]) {
-    const int4 *q = reinterpret_cast<const int4 *>(dp);
-    const int4 q1 = __ldg(q + 1), q2 = __ldg(q + 2), q3 = __ldg(q + 3);
-    oa[0] = q1.x; oa[1] = q1.y; oa[2] = q1.z; oa[3] = q1.w; oa[4] = q2.x; oa[5] = q2.y;
-    ob[0] = q2.z; ob[1] = q2.w; ob[2] = q3.x; ob[3] = q3.y; ob[4] = q3.z; ob[5] = q3.w;
-}
-__device__ __forceinline__ uint32_t fbits(float x) { return __float_as_uint(x); }
-
-// Storage formats of the check-to-variable messages (computation is FP32):
-// FP32, FP16 (round to nearest), or int8 codes q with m = q * qstep,
-// |q| <= 127 (values beyond saturate; the quantum is one scale for the one
-// stored edge type, heavy check-to-variable edges).
-template <typename M>
-struct Codec;
-template <>
-struct Codec<float> {
-    __device__ static float dec(float v, const Work &) { return v; }
-    __device__ static float enc(float v, const Work &) { return v; }
-};
-template <>
-struct Codec<__half> {
-    __device__ static float dec(__half v, const Work &) { return __half2float(v); }
-    __device__ static __half enc(float v, const Work &) { return __float2half_rn(v); }
-};
-template <>
-struct Codec<int8_t> {
-    __device__ static float dec(int8_t v, const Work &W) { return (float)v * W.qstep; }
-    __device__ static int8_t enc(float v, const Work &W) {
-        return (int8_t)__float2int_rn(fminf(fmaxf(v * W.qinv, -127.0f), 127.0f));
-    }
-};
-
 // ------------------------------------------------------------ kernels
 
 // Initial state: L = Q (heavy), phiq = +-Phi(|clip Q|) and the iteration-0
@@ -322,516 +123,6 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
         W.t[f] = 1;
     }
     if (tid == 0) *W.err = 0;
-}
-
-// ---- check-node pass
-//
-// Pass modes (uniform per launch): iteration 1 updates without reading old
-// messages; later iterations read them; the stop test of iteration t-1 runs
-// when t-1 >= et_start; the pass after the last iteration only tests.
-enum CnMode { kFirst = 0, kSteady = 1, kSteadyTest = 2, kTestOnly = 3 };
-
-// Any row shape up to MAXD circulants (heavy first), runtime degree with
-// predication; used for shapes the exact instantiations do not cover.
-template <int MAXD, typename M>
-__device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, int f, int r, int t,
-                                               int mode, int i0, int vpt) {
-    const bool update = mode != kTestOnly;
-    const bool read_msg = mode == kSteady || mode == kSteadyTest;
-    const bool test = mode == kSteadyTest || mode == kTestOnly;
-    const int Z = T.Z, ZW = W.ZW;
-    const int rp = T.row_ptr[r];
-    const int deg = T.row_ptr[r + 1] - rp;
-    const int nh = T.row_nh[r];
-    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
-    M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
-    const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
-    const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
-    const size_t bstride = (size_t)T.n_d1 * ZW;
-    uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
-    const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
-    const uint32_t *syn = W.syn + (size_t)f * W.words_m;
-    bool bad = false;
-    for (int u = 0; u < vpt; u++) {
-        const int i = i0 + u * kThreads;
-        const bool valid = i < Z;
-        const int cidx = r * Z + i;
-        const uint32_t sbit = __ldg(syn + min(cidx >> 5, (int)W.words_m - 1)) << (31 - (cidx & 31));
-        float phi[MAXD];
-        uint32_t sg[MAXD];
-        uint32_t stot = sbit, par = sbit;
-#pragma unroll
-        for (int k = 0; k < MAXD; k++) {
-            phi[k] = 0.0f;
-            sg[k] = 0;
-            if (k < deg) {
-                const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
-                if (k < nh) {
-                    const float lv = L[oa + i];
-                    par ^= fbits(lv);
-                    const float d = lv - (read_msg ? Codec<M>::dec(msg_rd[ob + i], W) : 0.0f);
-                    phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
-                    sg[k] = fbits(d);
-                } else {
-                    const float p = update ? __ldg(phiq + oa + i) : 0.0f;
-                    if (test) par ^= __ldg(bprev + ob + (i >> 5)) << (31 - (i & 31));
-                    phi[k] = fabsf(p);
-                    sg[k] = fbits(p);
-                }
-                stot ^= sg[k];
-            }
-        }
-        if (test) bad |= valid && (par & kSign) != 0;
-        if (!update) continue;
-        float pre[MAXD + 1], suf[MAXD + 1];
-        pre[0] = 0.0f;
-#pragma unroll
-        for (int k = 0; k < MAXD; k++) pre[k + 1] = pre[k] + phi[k];
-        suf[MAXD] = 0.0f;
-#pragma unroll
-        for (int k = MAXD - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
-#pragma unroll
-        for (int k = 0; k < MAXD; k++) {
-            if (k >= deg) break;
-            const qc::RowEnt e = T.rows[rp + k];
-            const int oa = T.row_off_a[rp + k], ob = T.row_off_b[rp + k];
-            const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
-            const uint32_t sk = (stot ^ sg[k]) & kSign;
-            if (k < nh) {
-                const float mag = fminf(psi_f(ex), W.clip);
-                if (valid) msg[ob + i] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
-            } else {
-                const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
-                const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
-                if ((threadIdx.x & 31) == 0 && valid) bcur[ob + (i >> 5)] = word;
-                if (W.soft && valid) {
-                    int vo = i + e.shift;
-                    if (vo >= Z) vo -= Z;
-                    const float mag = fminf(psi_f(ex), W.clip);
-                    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
-                    post1[oa + i] = W.llr[(size_t)f * W.n + (size_t)e.col * Z + vo] +
-                                    kLn2 * __uint_as_float(fbits(mag) ^ sk);
-                }
-            }
-        }
-    }
-    return bad;
-}
-
-// ---- check-node pass staged through shared memory by bulk async copies
-//
-// One block owns kTile consecutive checks (offsets i0 .. i0+kTile-1) of
-// one base row of one frame. Thread 0 arms an mbarrier and issues one
-// cp.async.bulk per operand row: the heavy posteriors at i0 + shift, the old
-// messages and the degree-1 psi values at i0, and the degree-1 decision
-// words of iteration t-1. Each source start is rounded down to 16 bytes
-// (the copy unit) and the remainder is added when reading. Every thread then
-// waits on the barrier (bounded) and evaluates its kTmaVpt checks, i0 + c *
-// kThreads + threadIdx.x, from shared memory: consecutive threads read
-// consecutive words, so the reads are free of bank conflicts.
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
-    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// Bytes to stage for `count` elements of `esize` bytes starting at `src`
-// once the start is rounded down to 16 bytes; *rem receives the offset of
-// src[0], in elements, from that rounded start.
-__device__ __forceinline__ uint32_t stage_bytes(const void *src, uint32_t count, int esize,
-                                                int *rem) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-    *rem = (int)((a & 15u) / (uintptr_t)esize);
-    return ((uint32_t)(*rem + count) * (uint32_t)esize + 15u) & ~15u;
-}
-
-// Bounded wait for the staged operands. On timeout the block records a
-// device error (decoding stops with converged = -1), waits once more
-// (bounded) for its copies, and reports failure.
-__device__ __forceinline__ bool stage_wait(uint64_t *bar, const Work &W) {
-    for (unsigned it = 0; it < kWaitLimit; it++)
-        if (mbar_try_wait(bar, 0)) return true;
-    atomicOr(W.err, 1);
-    for (unsigned it = 0; it < kWaitLimit; it++)
-        if (mbar_try_wait(bar, 0)) break;
-    return false;
-}
-
-// Soft output of a degree-1 neighbour (row entry e, check i) at iteration t:
-// its posterior Q_p + m_cp in natural units, where the message has sign sk
-// and psi-domain magnitude psi(ex) (clipped).
-__device__ __noinline__ void soft_deg1(const Table &T, const Work &W, int f, int t, int e, int i,
-                                       float ex, uint32_t sk) {
-    const int Z = T.Z;
-    const qc::RowEnt re = T.rows[e];
-    int vo = i + re.shift;
-    if (vo >= Z) vo -= Z;
-    const float mag = fminf(psi_f(ex), W.clip);
-    float *post1 = W.post1 + ((size_t)(t & 1) * W.n_frames + f) * T.n_d1 * Z;
-    post1[T.row_off_a[e] + i] =
-        W.llr[(size_t)f * W.n + (size_t)re.col * Z + vo] + kLn2 * __uint_as_float(fbits(mag) ^ sk);
-}
-
-template <int NH, int ND, int MODE, typename M>
-__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int rp, int t,
-                                        const qc::RowDesc *dp, unsigned char *smem) {
-    constexpr int D = NH + ND;
-    constexpr int NHa = NH > 0 ? NH : 1;
-    constexpr int NDa = ND > 0 ? ND : 1;
-    constexpr bool kUpdate = MODE != kTestOnly;
-    constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
-    constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
-    constexpr int kWordStep = kThreads / 32;
-    const int Z = T.Z, ZW = W.ZW;
-    int oa[qc::kDescEnts], ob[qc::kDescEnts];
-    load_offsets(dp, oa, ob);
-    const int i0 = blockIdx.x * kTile;
-    const int tid = threadIdx.x;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *s_off = reinterpret_cast<int *>(smem + 16);  // per staged row: start of its data
-    float *stage = reinterpret_cast<float *>(smem + kSmemHeader);
-    const size_t bstride = (size_t)T.n_d1 * ZW;
-    // messages of iteration t-1 (read) and t (written); one buffer when flooding
-    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
-    M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
-
-    // Thread 0: arm the barrier, publish each staged row's read offset
-    // (row slot * kStage + 16-byte remainder), then issue the copies.
-    // Staged rows: NH posteriors, NH old messages (kReadMsg), ND psi values
-    // (kUpdate), then ND decision-word rows of kStageWords words (kTest).
-    if (tid == 0) {
-        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
-        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
-        const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
-        mbar_init(bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const void *src[2 * NHa + 2 * NDa];
-        uint32_t nb[2 * NHa + 2 * NDa];
-        int slot_start[2 * NHa + 2 * NDa];
-        int ncopy = 0, pos = 0;
-        uint32_t total = 0;
-        // Each staged row takes row_slots 4-byte slots; s_off holds the row's
-        // first element in units of its own element size.
-        auto add = [&](const void *p, uint32_t count, int esize, int row_slots) {
-            int rem;
-            nb[ncopy] = stage_bytes(p, count, esize, &rem);
-            src[ncopy] = reinterpret_cast<const char *>(p) - esize * rem;
-            slot_start[ncopy] = pos;
-            s_off[ncopy] = pos * (4 / esize) + rem;
-            total += nb[ncopy];
-            pos += row_slots;
-            ncopy++;
-        };
-#pragma unroll
-        for (int k = 0; k < NH; k++) add(L + oa[k] + i0, kTile, 4, kStage);
-        if (kReadMsg) {
-#pragma unroll
-            for (int k = 0; k < NH; k++)
-                add(msg_rd + ob[k] + i0, kTile, (int)sizeof(M), kStage);
-        }
-        if (kUpdate) {
-#pragma unroll
-            for (int k = 0; k < ND; k++) add(phiq + oa[NH + k] + i0, kTile, 4, kStage);
-        }
-        if (kTest) {
-#pragma unroll
-            for (int k = 0; k < ND; k++)
-                add(bprev + ob[NH + k] + (i0 >> 5), kTile / 32, 4, kStageWords);
-        }
-        mbar_expect_tx(bar, total);
-        for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
-    }
-    __syncthreads();  // barrier initialised, offsets published
-
-    // Per-row pointers for this thread's first check; check c sits at
-    // + c * kThreads elements (or + c * kWordStep words).
-    const float *pL[NHa], *pP[NDa];
-    const M *pM[NHa];
-    const uint32_t *pB[NDa];
-    {
-        int q = 0;
-#pragma unroll
-        for (int k = 0; k < NH; k++) pL[k] = stage + s_off[q++] + tid;
-        if (kReadMsg) {
-#pragma unroll
-            for (int k = 0; k < NH; k++) pM[k] = reinterpret_cast<const M *>(stage) + s_off[q++] + tid;
-        }
-        if (kUpdate) {
-#pragma unroll
-            for (int k = 0; k < ND; k++) pP[k] = stage + s_off[q++] + tid;
-        }
-        if (kTest) {
-#pragma unroll
-            for (int k = 0; k < ND; k++)
-                pB[k] = reinterpret_cast<const uint32_t *>(stage) + s_off[q++] + (tid >> 5);
-        }
-    }
-    // Output rows at this thread's first check.
-    M *oM[NHa];
-    uint32_t *oB[NDa];
-    {
-        uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
-#pragma unroll
-        for (int k = 0; k < D; k++) {
-            if (k < NH) oM[k] = msg + ob[k] + i0 + tid;
-            else oB[k - NH] = bcur + ob[k] + (i0 >> 5) + (tid >> 5);
-        }
-    }
-    const int c0 = r * Z + i0 + tid;
-    const uint32_t *sy = W.syn + (size_t)f * W.words_m + (c0 >> 5);
-    const int ssh = 31 - (c0 & 31);
-    const int dsh = 31 - (tid & 31);
-    const bool lane0 = (tid & 31) == 0;
-
-    // syndrome words of the owned checks, loaded while the copies are in flight
-    uint32_t sw[kTmaVpt];
-#pragma unroll
-    for (int c = 0; c < kTmaVpt; c++)
-        sw[c] = i0 + c * kThreads + tid < Z ? (__ldg(sy + c * kWordStep) << ssh) : 0u;
-
-    const bool staged = stage_wait(bar, W);
-    bool bad = false;
-    if (staged) {
-      if constexpr (QCLDPC_CN_PAIR && kTmaVpt % 2 == 0) {
-        // Two checks (c, c + 1) per step, their arithmetic in packed FP32x2
-        // operations (per lane identical to the scalar path below).
-#pragma unroll kCnUnroll
-        for (int c = 0; c < kTmaVpt; c += 2) {
-            const int ia = i0 + c * kThreads + tid, ib = ia + kThreads;
-            const bool va = ia < Z, vb = ib < Z;
-            float2 lv[NHa], phi[D];
-            uint32_t sga[D], sgb[D];
-            uint32_t sta = sw[c], stb = sw[c + 1], pa = sw[c], pb = sw[c + 1];
-#pragma unroll
-            for (int k = 0; k < NH; k++) {
-                lv[k] = make_float2(pL[k][c * kThreads], pL[k][(c + 1) * kThreads]);
-                pa ^= fbits(lv[k].x);
-                pb ^= fbits(lv[k].y);
-            }
-            if (kTest) {
-#pragma unroll
-                for (int k = 0; k < ND; k++) {
-                    pa ^= pB[k][c * kWordStep] << dsh;
-                    pb ^= pB[k][(c + 1) * kWordStep] << dsh;
-                }
-                bad |= (va && (pa & kSign) != 0) || (vb && (pb & kSign) != 0);
-            }
-            if constexpr (kUpdate) {
-#pragma unroll
-                for (int k = 0; k < NH; k++) {
-                    float2 d = lv[k];
-                    if (kReadMsg) {
-                        const float2 m = make_float2(Codec<M>::dec(pM[k][c * kThreads], W),
-                                                     Codec<M>::dec(pM[k][(c + 1) * kThreads], W));
-                        d = __ffma2_rn(m, f2(-1.0f), d);  // lv - m, one rounding
-                    }
-                    phi[k] = psi2(make_float2(fminf(fmaxf(fabsf(d.x), W.xmin), W.clip),
-                                              fminf(fmaxf(fabsf(d.y), W.xmin), W.clip)));
-                    sga[k] = fbits(d.x);
-                    sgb[k] = fbits(d.y);
-                    sta ^= sga[k];
-                    stb ^= sgb[k];
-                }
-#pragma unroll
-                for (int k = 0; k < ND; k++) {
-                    const float qa = pP[k][c * kThreads], qb = pP[k][(c + 1) * kThreads];
-                    phi[NH + k] = make_float2(fabsf(qa), fabsf(qb));
-                    sga[NH + k] = fbits(qa);
-                    sgb[NH + k] = fbits(qb);
-                    sta ^= sga[NH + k];
-                    stb ^= sgb[NH + k];
-                }
-                // exclusive sums by prefix / suffix (psi >= +0, so 0 + x = x)
-                float2 pre[D], suf[D];
-                pre[0] = phi[0];
-#pragma unroll
-                for (int k = 1; k < D; k++) pre[k] = __fadd2_rn(pre[k - 1], phi[k]);
-                suf[D - 1] = phi[D - 1];
-#pragma unroll
-                for (int k = D - 2; k >= 0; k--) suf[k] = __fadd2_rn(suf[k + 1], phi[k]);
-#pragma unroll
-                for (int k = 0; k < D; k++) {
-                    const float2 s2 = k == 0       ? suf[1]
-                                      : k == D - 1 ? pre[D - 2]
-                                                   : __fadd2_rn(pre[k - 1], suf[k + 1]);
-                    const float2 ex = make_float2(fmaxf(s2.x, W.xmin), fmaxf(s2.y, W.xmin));
-                    const uint32_t ska = (sta ^ sga[k]) & kSign, skb = (stb ^ sgb[k]) & kSign;
-                    if (k < NH) {
-                        const float2 mag = psi2(ex);
-                        if (va) oM[k][c * kThreads] =
-                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.x, W.clip)) ^ ska), W);
-                        if (vb) oM[k][(c + 1) * kThreads] =
-                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.y, W.clip)) ^ skb), W);
-                    } else {
-                        const uint32_t da = ex.x < phi[k].x ? ska : (sga[k] & kSign);
-                        const uint32_t db = ex.y < phi[k].y ? skb : (sgb[k] & kSign);
-                        const uint32_t wa = __ballot_sync(0xffffffffu, va && da != 0);
-                        const uint32_t wb = __ballot_sync(0xffffffffu, vb && db != 0);
-                        if (lane0 && va) oB[k - NH][c * kWordStep] = wa;
-                        if (lane0 && vb) oB[k - NH][(c + 1) * kWordStep] = wb;
-                        if (W.soft) {
-                            if (va) soft_deg1(T, W, f, t, rp + k, ia, ex.x, ska);
-                            if (vb) soft_deg1(T, W, f, t, rp + k, ib, ex.y, skb);
-                        }
-                    }
-                }
-            }
-        }
-      } else {
-#pragma unroll kCnUnroll
-        for (int c = 0; c < kTmaVpt; c++) {
-            const int i = i0 + c * kThreads + tid;
-            const bool valid = i < Z;
-            const uint32_t sb = sw[c];
-            float lv[NHa], phi[D];
-            uint32_t sg[D];
-            uint32_t stot = sb, par = sb;
-#pragma unroll
-            for (int k = 0; k < NH; k++) {
-                lv[k] = pL[k][c * kThreads];
-                par ^= fbits(lv[k]);
-            }
-            if (kTest) {
-#pragma unroll
-                for (int k = 0; k < ND; k++) par ^= pB[k][c * kWordStep] << dsh;
-                bad |= valid && (par & kSign) != 0;
-            }
-            if constexpr (kUpdate) {
-#pragma unroll
-                for (int k = 0; k < NH; k++) {
-                    const float d = lv[k] - (kReadMsg ? Codec<M>::dec(pM[k][c * kThreads], W) : 0.0f);
-                    phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
-                    sg[k] = fbits(d);
-                    stot ^= sg[k];
-                }
-#pragma unroll
-                for (int k = 0; k < ND; k++) {
-                    const float p = pP[k][c * kThreads];
-                    phi[NH + k] = fabsf(p);
-                    sg[NH + k] = fbits(p);
-                    stot ^= sg[NH + k];
-                }
-                float pre[D + 1], suf[D + 1];
-                pre[0] = 0.0f;
-#pragma unroll
-                for (int k = 0; k < D; k++) pre[k + 1] = pre[k] + phi[k];
-                suf[D] = 0.0f;
-#pragma unroll
-                for (int k = D - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
-#pragma unroll
-                for (int k = 0; k < D; k++) {
-                    const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
-                    const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
-                    if (k < NH) {
-                        const float mag = fminf(psi_f(ex), W.clip);
-                        if (valid) oM[k][c * kThreads] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
-                    } else {
-                        const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
-                        const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
-                        if (lane0 && valid) oB[k - NH][c * kWordStep] = word;
-                        if (W.soft && valid) soft_deg1(T, W, f, t, rp + k, i, ex, sk);
-                    }
-                }
-            }
-        }
-      }
-    }
-    __syncthreads();
-    if (tid == 0) mbar_inval(bar);
-    return bad;
-}
-
-template <int MODE, typename M>
-__device__ __forceinline__ bool cn_tile_dispatch(const Table &T, const Work &W, int f, int r, int t,
-                                                 int rp, int nh, int nd, const qc::RowDesc *dp,
-                                                 unsigned char *smem) {
-    switch (nh * 4 + nd) {
-        case 1 * 4 + 1: return cn_tile<1, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 2 * 4 + 0: return cn_tile<2, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 2 * 4 + 1: return cn_tile<2, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 3 * 4 + 0: return cn_tile<3, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 3 * 4 + 1: return cn_tile<3, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 4 * 4 + 0: return cn_tile<4, 0, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        case 4 * 4 + 1: return cn_tile<4, 1, MODE, M>(T, W, f, r, rp, t, dp, smem);
-        default: return false;
-    }
-}
-
-
-// Check-node pass of iteration t, staged variant: grid (ceil(Z / kTile), base
-// row, frame), dynamic shared memory sized by cn_tma_smem for the code's
-// widest exact-shape row. Rows of other shapes take the generic path.
-template <int MAXD, typename M>
-__global__ void __launch_bounds__(kThreads, QCLDPC_CN_TMA_MINBLOCKS) cn_tma_kernel(const __grid_constant__ Table T,
-                                                          const __grid_constant__ Work W) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    pdl_launch_dependents();  // the control step may be scheduled; it waits for this pass
-    const int f = blockIdx.z;
-    if (W.active[f] == 0) return;  // block-uniform
-    const bool group = W.pass == kPassGroup;
-    const qc::RowDesc *dp = group ? T.row_desc + (W.lrow0 + (int)blockIdx.y) : T.row_desc_ord + blockIdx.y;
-    const int4 head = __ldg(reinterpret_cast<const int4 *>(dp));  // r, rp, nh, nd
-    const int r = head.x;
-    const int t = W.t[f] - (group ? 1 : 0);
-    int mode = t > W.max_iter ? kTestOnly
-               : t == 1       ? kFirst
-               : (t - 1 >= W.et_start) ? kSteadyTest : kSteady;
-    if (W.pass == kPassTest) {
-        if (mode != kSteadyTest && mode != kTestOnly) return;  // no test due
-        mode = kTestOnly;
-    } else if (group) {
-        if (mode == kTestOnly) return;
-        if (mode == kSteadyTest) mode = kSteady;
-    }
-    const int rp = head.y, nh = head.z, nd = head.w;
-    bool bad;
-    if (exact_shape(nh, nd)) {
-        switch (mode) {
-            case kFirst: bad = cn_tile_dispatch<kFirst, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
-            case kSteady: bad = cn_tile_dispatch<kSteady, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
-            case kSteadyTest: bad = cn_tile_dispatch<kSteadyTest, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
-            default: bad = cn_tile_dispatch<kTestOnly, M>(T, W, f, r, t, rp, nh, nd, dp, smem); break;
-        }
-    } else {
-        bad = cn_row_generic<MAXD, M>(T, W, f, r, t, mode, blockIdx.x * kTile + threadIdx.x, kTmaVpt);
-    }
-    if (mode == kSteadyTest || mode == kTestOnly) {
-        if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;
-    }
 }
 
 // Loop control, one block: apply each frame's stop test of its iteration
@@ -1142,17 +433,12 @@ int sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-template <typename M>
-void *cn_tma_kernel_for_fmt(int maxdeg) {
-    if (maxdeg <= 5) return (void *)cn_tma_kernel<5, M>;
-    if (maxdeg <= 8) return (void *)cn_tma_kernel<8, M>;
-    return (void *)cn_tma_kernel<16, M>;
-}
-
-void *cn_tma_kernel_for(int maxdeg, int fmt) {
-    if (fmt == 1) return cn_tma_kernel_for_fmt<__half>(maxdeg);
-    if (fmt == 2) return cn_tma_kernel_for_fmt<int8_t>(maxdeg);
-    return cn_tma_kernel_for_fmt<float>(maxdeg);
+// The check-pass kernel for a message format (its translation unit): full
+// kThreads-thread blocks, or blocks of any width (nt < kThreads).
+void *cn_tma_kernel_for(int maxdeg, int fmt, int nt) {
+    if (fmt == 1) return qc::cn_kernel_f16(maxdeg, nt);
+    if (fmt == 2) return qc::cn_kernel_i8(maxdeg, nt);
+    return qc::cn_kernel_f32(maxdeg, nt);
 }
 
 void *lvn_kernel_for(int fmt) {
@@ -1168,38 +454,44 @@ void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
     *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
-
-template <typename M>
-void raise_smem_cap(int cap) {
-    cudaFuncSetAttribute((const void *)cn_tma_kernel<5, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    cudaFuncSetAttribute((const void *)cn_tma_kernel<8, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    cudaFuncSetAttribute((const void *)cn_tma_kernel<16, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-}
-
 // Launch of the check-node pass for a code: kernel, grid and dynamic shared
 // memory (the staged variant needs the code's widest exact-shape row).
 struct CnLaunch {
     void *func;
     dim3 grid;
+    dim3 block;
     size_t smem;
 };
+
+// Threads per check block: the fewest warps whose tile (threads x kTmaVpt
+// checks) still covers a row in as many blocks as kTile-check tiles would.
+// A row of Z = 625 gets 160 threads (one 640-check tile, not 61% of a
+// 1024-check one), and smaller blocks leave room for more of them per SM.
+int cn_threads(int Z) {
+    if (!QCLDPC_CN_FIT) return kThreads;
+    const int nblk = (Z + kTile - 1) / kTile;
+    const int per = (Z + nblk - 1) / nblk;
+    return std::min(kThreads, 32 * ((per + 32 * kTmaVpt - 1) / (32 * kTmaVpt)));
+}
 
 CnLaunch cn_launch(const Table &T, int F, int fmt) {
     CnLaunch c;
     {
+        const int nt = cn_threads(T.Z), tile = nt * kTmaVpt;
         // the code's widest exact-shape row (its staged rows and word rows)
-        const size_t smem = kSmemHeader + (size_t)T.stage_rows_max * kStage * 4 +
-                            (size_t)T.stage_words_max * kStageWords * 4;
-        c.func = cn_tma_kernel_for(T.max_row_deg, fmt);
-        c.grid = dim3((unsigned)((T.Z + kTile - 1) / kTile), (unsigned)T.mb, (unsigned)F);
+        const size_t smem = kSmemHeader + (size_t)T.stage_rows_max * (tile + 4) * 4 +
+                            (size_t)T.stage_words_max * (tile / 32 + 4) * 4;
+        c.func = cn_tma_kernel_for(T.max_row_deg, fmt, nt);
+        c.grid = dim3((unsigned)((T.Z + tile - 1) / tile), (unsigned)T.mb, (unsigned)F);
+        c.block = dim3((unsigned)nt);
         c.smem = smem;
         // Capacity for the largest staged row set (4 heavy + 1 degree-1).
         static std::once_flag once;
         std::call_once(once, [] {
             const int cap = kSmemHeader + 9 * kStage * 4 + kStageWords * 4;
-            raise_smem_cap<float>(cap);
-            raise_smem_cap<__half>(cap);
-            raise_smem_cap<int8_t>(cap);
+            qc::cn_smem_cap_f32(cap);
+            qc::cn_smem_cap_f16(cap);
+            qc::cn_smem_cap_i8(cap);
         });
     }
     return c;
@@ -1268,7 +560,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
     const CnLaunch cl = cn_launch(T, F, w0.fmt);
     cudaError_t err;
     if (w0.layered) wcopy.pass = kPassTest;
-    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, dim3(kThreads), args,
+    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, cl.block, args,
                           cl.smem)) != cudaSuccess)
         return err;
     void *ctrl_args[] = {&wcopy, &handle};
@@ -1291,7 +583,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
         dim3 grid = cl.grid;
         grid.y = (unsigned)wg.lrows;
         cudaGraphNode_t a, b;
-        if ((err = add_kernel(&a, body, &prev, 1, cl.func, grid, dim3(kThreads), gargs,
+        if ((err = add_kernel(&a, body, &prev, 1, cl.func, grid, cl.block, gargs,
                               cl.smem)) != cudaSuccess ||
             (err = add_kernel(&b, body, &a, 1, lvn_kernel_for(w0.fmt), vn_grid(T, F),
                               dim3(kThreads), gargs)) != cudaSuccess)
@@ -1355,7 +647,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
     cudaGraphConditionalHandle none = 0;
     cudaError_t err = cudaGetLastError();
     for (int t = 1; t <= w.max_iter + 1 && err == cudaSuccess; t++) {
-        err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
+        err = cudaLaunchKernel(cl.func, cl.grid, cl.block, args, cl.smem, stream);
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
         if (t <= w.max_iter && !w.layered) {
@@ -1372,7 +664,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
             void *gargs[] = {&tcopy, &wg};
             dim3 grid = cl.grid;
             grid.y = (unsigned)wg.lrows;
-            err = cudaLaunchKernel(cl.func, grid, dim3(kThreads), gargs, cl.smem, stream);
+            err = cudaLaunchKernel(cl.func, grid, cl.block, gargs, cl.smem, stream);
             if (err == cudaSuccess)
                 err = cudaLaunchKernel(lvn_kernel_for(w.fmt), vn_grid(T, F), dim3(kThreads), gargs,
                                        0, stream);
@@ -1637,7 +929,7 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     void *args[] = {&tcopy, &w};
     cudaEventRecord(ev[0], stream);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel(cl.func, cl.grid, dim3(kThreads), args, cl.smem, stream);
+        err = cudaLaunchKernel(cl.func, cl.grid, cl.block, args, cl.smem, stream);
     cudaEventRecord(ev[1], stream);
     qc::ColsInline ccopy = code->cols_in;
     void *vn_args[] = {&tcopy, &w, &ccopy};
@@ -1857,7 +1149,7 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < n_passes && err == cudaSuccess; i++) {
         cudaGraphNode_t a, b, c;
-        err = add_kernel(&a, g, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, dim3(kThreads),
+        err = add_kernel(&a, g, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
                          args, cl.smem);
         if (err == cudaSuccess)
             err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),

@@ -257,6 +257,23 @@ def test_decode_zero_iterations_returns_channel_decisions():
         assert_posteriors_close(post[f], ref)
 
 
+@pytest.mark.parametrize("Z", [700, 1500, 2000, 2052])
+def test_check_block_widths_match_oracle(Z):
+    """The check pass sizes its blocks to Z: 1024-check tiles when those fill
+    the row (Z = 2000: two tiles, the second 976 checks), else the fewest
+    warps that cover the row in as many tiles (Z = 700: one 768-check tile of
+    192 threads; Z = 1500: two, the second 732 checks; Z = 2052: three, the
+    last 516 checks). Soft output and the stop test on both kernel forms."""
+    fr = make_frames(synth.rate002_code(Z), 0.12, 2)
+    code = q.create_code_from(fr.code_dict)
+    iters = 12
+    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, fr.F, iters, et_start=6)
+    for f in range(fr.F):
+        ref, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], iters, et_start=6)
+        assert (its[f], conv[f]) == (it, int(cv)), f"Z={Z} frame {f}"
+        assert_posteriors_close(post[f], ref, f"Z={Z} frame {f}")
+
+
 @pytest.mark.parametrize("Z", [1, 2, 5, 37, 100])
 def test_decode_ragged_and_irregular_codes(Z):
     d = odd_code(Z)
