@@ -210,8 +210,11 @@ def source_hash():
     removed: the committed DRAM counters stay valid across comment edits and
     are dropped once the code itself changes."""
     h = hashlib.sha256()
-    for f in ("decode.cu", "qcldpc_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1702_07740_gb300", "csrc", f)) as fh:
+    csrc = os.path.join(ROOT, "paper_1702_07740_gb300", "csrc")
+    files = sorted(f for f in os.listdir(csrc)
+                   if f.endswith(".cuh") or f == "decode.cu" or f.startswith("check_pass"))
+    for f in files:
+        with open(os.path.join(csrc, f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
@@ -219,17 +222,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(pass_name: str, msg_format: str, frames: int):
-    """(kernel name, per-launch DRAM bytes) of a decoder pass from the
-    committed ncu summary, or (None, None) when the kernel source changed
-    since the capture or the capture was of another configuration."""
+def ncu_traffic(pass_name: str, code: str, msg_format: str, frames: int):
+    """(kernel name, per-launch DRAM bytes) of a decoder pass on a code from
+    the committed ncu summary (entries keyed "<code>:<pass>"), or (None,
+    None) when the kernel source changed since the capture or the capture was
+    of another configuration."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None, None
-    e = d.get(pass_name)
+    e = d.get(f"{code}:{pass_name}")
     if (not e or e.get("source_hash") != source_hash() or e.get("msg_format", "fp32") != msg_format
             or e.get("frames") != frames):
         return None, None
@@ -459,7 +463,7 @@ def run_ours(args, world, rank, local):
                               else ("variable_pass", vn_ms, vn_b * F))
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    kname, traffic = ncu_traffic(dom, args.msg_format, F)
+    kname, traffic = ncu_traffic(dom, args.code, args.msg_format, F)
     iter_ms = cn_ms + vn_ms
     if rank != 0:
         if world > 1:

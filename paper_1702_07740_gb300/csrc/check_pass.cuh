@@ -3,7 +3,7 @@
 // check_pass_f32.cu, check_pass_f16.cu and check_pass_i8.cu, which export
 // its kernels through qc::cn_kernel_<format>.
 //
-// Each kernel comes in two block shapes: NT = kThreads (compile-time strides,
+// Each kernel comes in two block shapes: NT = kCnThreads (compile-time strides,
 // rows of Z > (kTile - kTile / 4) checks), and NT = 0, which reads its width
 // from blockDim.x (the launch sizes short rows to fit; the run-time strides
 // cost registers, so full rows keep the first form).
@@ -207,7 +207,7 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     const int Z = T.Z, ZW = W.ZW;
     int oa[qc::kDescEnts], ob[qc::kDescEnts];
     load_offsets(dp, oa, ob);
-    const int nt = NT ? NT : (int)blockDim.x;  // threads: a multiple of 32, at most kThreads
+    const int nt = NT ? NT : (int)blockDim.x;  // threads: a multiple of 32, at most kCnThreads
     const int ws = nt >> 5;            // decision words per check slot
     const int tile = nt * kTmaVpt;     // checks per block
     const int i0 = blockIdx.x * tile;
@@ -494,7 +494,7 @@ __device__ __forceinline__ bool cn_tile_dispatch(const Table &T, const Work &W, 
 // sized by cn_launch for the code's widest exact-shape row. Rows of other
 // shapes take the generic path.
 template <int MAXD, typename M, int NT>
-__global__ void __launch_bounds__(kThreads, NT ? QCLDPC_CN_TMA_MINBLOCKS : QCLDPC_CN_FIT_MINBLOCKS)
+__global__ void __launch_bounds__(kCnThreads, NT ? QCLDPC_CN_TMA_MINBLOCKS : QCLDPC_CN_FIT_MINBLOCKS)
     cn_tma_kernel(const __grid_constant__ Table T, const __grid_constant__ Work W) {
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_launch_dependents();  // the control step may be scheduled; it waits for this pass
@@ -536,10 +536,10 @@ __global__ void __launch_bounds__(kThreads, NT ? QCLDPC_CN_TMA_MINBLOCKS : QCLDP
 
 template <typename M>
 void *cn_kernel_select(int maxdeg, int nt) {
-    if (nt == kThreads) {
-        if (maxdeg <= 5) return (void *)cn_tma_kernel<5, M, kThreads>;
-        if (maxdeg <= 8) return (void *)cn_tma_kernel<8, M, kThreads>;
-        return (void *)cn_tma_kernel<16, M, kThreads>;
+    if (nt == kCnThreads) {
+        if (maxdeg <= 5) return (void *)cn_tma_kernel<5, M, kCnThreads>;
+        if (maxdeg <= 8) return (void *)cn_tma_kernel<8, M, kCnThreads>;
+        return (void *)cn_tma_kernel<16, M, kCnThreads>;
     }
     if (maxdeg <= 5) return (void *)cn_tma_kernel<5, M, 0>;
     if (maxdeg <= 8) return (void *)cn_tma_kernel<8, M, 0>;
@@ -548,8 +548,8 @@ void *cn_kernel_select(int maxdeg, int nt) {
 
 template <typename M>
 void cn_raise_smem_cap(int cap) {
-    const void *k[] = {(const void *)cn_tma_kernel<5, M, kThreads>, (const void *)cn_tma_kernel<8, M, kThreads>,
-                       (const void *)cn_tma_kernel<16, M, kThreads>, (const void *)cn_tma_kernel<5, M, 0>,
+    const void *k[] = {(const void *)cn_tma_kernel<5, M, kCnThreads>, (const void *)cn_tma_kernel<8, M, kCnThreads>,
+                       (const void *)cn_tma_kernel<16, M, kCnThreads>, (const void *)cn_tma_kernel<5, M, 0>,
                        (const void *)cn_tma_kernel<8, M, 0>, (const void *)cn_tma_kernel<16, M, 0>};
     for (const void *f : k) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
 }

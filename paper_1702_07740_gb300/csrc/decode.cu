@@ -468,10 +468,10 @@ struct CnLaunch {
 // A row of Z = 625 gets 160 threads (one 640-check tile, not 61% of a
 // 1024-check one), and smaller blocks leave room for more of them per SM.
 int cn_threads(int Z) {
-    if (!QCLDPC_CN_FIT) return kThreads;
+    if (!QCLDPC_CN_FIT) return kCnThreads;
     const int nblk = (Z + kTile - 1) / kTile;
     const int per = (Z + nblk - 1) / nblk;
-    return std::min(kThreads, 32 * ((per + 32 * kTmaVpt - 1) / (32 * kTmaVpt)));
+    return std::min(kCnThreads, 32 * ((per + 32 * kTmaVpt - 1) / (32 * kTmaVpt)));
 }
 
 CnLaunch cn_launch(const Table &T, int F, int fmt) {

@@ -36,7 +36,13 @@ constexpr int kGraphCacheSize = 8;
 #define QCLDPC_CN_TVPT 4
 #endif
 constexpr int kTmaVpt = QCLDPC_CN_TVPT;
-// Resident blocks per SM the staged pass is compiled for (caps registers).
+// Threads of a full check block.
+#ifndef QCLDPC_CN_THREADS
+#define QCLDPC_CN_THREADS 256
+#endif
+constexpr int kCnThreads = QCLDPC_CN_THREADS;
+// Resident full check blocks per SM the staged pass is compiled for (caps
+// registers).
 #ifndef QCLDPC_CN_TMA_MINBLOCKS
 #define QCLDPC_CN_TMA_MINBLOCKS 5
 #endif
@@ -54,16 +60,16 @@ constexpr int kTmaVpt = QCLDPC_CN_TVPT;
 #define QCLDPC_CN_UNROLL 4
 #endif
 constexpr int kCnUnroll = QCLDPC_CN_UNROLL;
-// Size check blocks to Z (cn_threads); 0 keeps kThreads for every code.
+// Size check blocks to Z (cn_threads); 0 keeps kCnThreads for every code.
 #ifndef QCLDPC_CN_FIT
 #define QCLDPC_CN_FIT 1
 #endif
-// Register cap of the variable-width check kernel, as resident 256-thread
+// Register cap of the variable-width check kernel, as resident full-width
 // blocks per SM (its narrower blocks fit more).
 #ifndef QCLDPC_CN_FIT_MINBLOCKS
 #define QCLDPC_CN_FIT_MINBLOCKS QCLDPC_CN_TMA_MINBLOCKS
 #endif
-constexpr int kTile = kThreads * kTmaVpt;      // checks per block, at most
+constexpr int kTile = kCnThreads * kTmaVpt;    // checks per block, at most
 constexpr int kStage = kTile + 4;              // staged floats per row (16-byte realignment)
 constexpr int kStageWords = kTile / 32 + 4;    // staged decision words per row
 constexpr int kSmemHeader = 128;               // mbarrier, then 16-byte aligned rows
@@ -227,7 +233,7 @@ struct Codec<int8_t> {
 namespace qc {
 // Check-pass kernels of one storage format (FP32, FP16, int8) for codes whose
 // rows have at most maxdeg circulants: the full-block kernel when nt ==
-// kThreads, else the one that takes its width from the launch.
+// kCnThreads, else the one that takes its width from the launch.
 void *cn_kernel_f32(int maxdeg, int nt);
 void *cn_kernel_f16(int maxdeg, int nt);
 void *cn_kernel_i8(int maxdeg, int nt);
