@@ -176,10 +176,16 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 // Grid (tile, heavy column, frame). Lanes past the end of the column read
 // message padding (never stored); the channel LLRs, the caller's buffer, are
 // read only in range.
+// Each thread keeps kVnParts independent partial sums per node, part p over
+// the column's circulants p, p + kVnParts, ... in order (part 0 starts from
+// Q_v), and adds them in part order at the end: the chains hide the load
+// latency of small batches, and the order is fixed, so a frame's result does
+// not depend on the launch shape or the batch it is decoded in.
 template <typename M, int VPT>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
                                                       const __grid_constant__ Work W,
                                                       const __grid_constant__ qc::ColsInline C) {
+    constexpr int P = kVnParts;
     pdl_wait();  // the control step's flags are complete and visible
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;
@@ -189,28 +195,46 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     const M *__restrict__ msg = static_cast<const M *>(W.msg) + (size_t)f * T.n_h * Z;
     const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
     float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
-    float acc[VPT];
+    float acc[VPT][P];
 #pragma unroll
     for (int u = 0; u < VPT; u++) {
         const int j = j0 + u * kThreads;
-        acc[u] = j < Z ? __ldg(q + j) * kLog2e : 0.0f;
-    }
-    if (C.ok) {
-        // the column's circulants from the inline copy (constant bank)
-        const int ce = C.col_ptr[hc + 1];
-#pragma unroll kVnUnroll
-        for (int k = C.col_ptr[hc]; k < ce; k++) {
-            const qc::ColEnt e = C.cols[k];
-            const M *__restrict__ mk = msg + e.id * Z;
 #pragma unroll
-            for (int u = 0; u < VPT; u++) {
-                int idx = j0 + u * kThreads - e.shift;
-                if (idx < 0) idx += Z;
-                acc[u] += Codec<M>::dec(mk[idx], W);
+        for (int p = 0; p < P; p++) acc[u][p] = (p == 0 && j < Z) ? __ldg(q + j) * kLog2e : 0.0f;
+    }
+    // add circulant (shift, id) to part p
+    auto add = [&](int shift, int id, int p) {
+        const M *__restrict__ mk = msg + id * Z;
+#pragma unroll
+        for (int u = 0; u < VPT; u++) {
+            int idx = j0 + u * kThreads - shift;
+            if (idx < 0) idx += Z;
+            acc[u][p] += Codec<M>::dec(mk[idx], W);
+        }
+    };
+    if (C.ok) {
+        // the column's circulants from the inline copy (constant bank):
+        // whole steps of P circulants, then the remainder
+        const int cb = C.col_ptr[hc], ce = C.col_ptr[hc + 1];
+        int k = cb;
+#pragma unroll kVnUnroll
+        for (; k + P <= ce; k += P) {
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                const qc::ColEnt e = C.cols[k + p];
+                add(e.shift, e.id, p);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P - 1; p++) {
+            if (k + p < ce) {
+                const qc::ColEnt e = C.cols[k + p];
+                add(e.shift, e.id, p);
             }
         }
     } else {
     // the column's circulants (shift, id), staged in shared memory in chunks
+    // of kColChunk (a multiple of P, so a chunk offset keeps the part of k)
     __shared__ int2 s_cols[kColChunk];
     const int cb = T.col_ptr[hc], ce = T.col_ptr[hc + 1];
     for (int base = cb; base < ce; base += kColChunk) {
@@ -219,15 +243,20 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
         if ((int)threadIdx.x < cnt)
             s_cols[threadIdx.x] = __ldg(reinterpret_cast<const int2 *>(T.cols) + base + threadIdx.x);
         __syncthreads();
-#pragma unroll kVnUnroll
-        for (int kk = 0; kk < cnt; kk++) {
-            const int2 e = s_cols[kk];  // (shift, id)
-            const M *__restrict__ mk = msg + e.y * Z;
+        int kk = 0;
+#pragma unroll kVnUnrollStaged
+        for (; kk + P <= cnt; kk += P) {
 #pragma unroll
-            for (int u = 0; u < VPT; u++) {
-                int idx = j0 + u * kThreads - e.x;
-                if (idx < 0) idx += Z;
-                acc[u] += Codec<M>::dec(mk[idx], W);
+            for (int p = 0; p < P; p++) {
+                const int2 e = s_cols[kk + p];
+                add(e.x, e.y, p);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P - 1; p++) {
+            if (kk + p < cnt) {
+                const int2 e = s_cols[kk + p];
+                add(e.x, e.y, p);
             }
         }
     }
@@ -236,7 +265,10 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     for (int u = 0; u < VPT; u++) {
         const int j = j0 + u * kThreads;
         if (j < Z) {
-            const float lvj = acc[u] + 0.0f;  // -0 -> +0: sgn(0) = +1 everywhere
+            float lvj = acc[u][0];
+#pragma unroll
+            for (int p = 1; p < P; p++) lvj += acc[u][p];
+            lvj += 0.0f;  // -0 -> +0: sgn(0) = +1 everywhere
             L[j] = lvj;
             L[j + Z] = lvj;
         }
@@ -403,11 +435,13 @@ void *vn_kernel_vpt(int vpt) {
 
 int sm_count();
 
+// Variable-pass launch: the nodes per thread (VPT) is the largest of
+// kVnVptMax ... 1 that still leaves four blocks per SM.
 VnLaunch vn_launch(const Table &T, int F, int fmt) {
     const int hc = std::max(T.n_hcols, 1);
     const long long want = 4LL * sm_count();
     int vpt = 1;
-    for (int v = 3; v >= 1; v--) {
+    for (int v = kVnVptMax; v >= 1; v--) {
         const long long blocks = (long long)F * hc * ((T.Z + kThreads * v - 1) / (kThreads * v));
         if (blocks >= want || v == 1) {
             vpt = v;

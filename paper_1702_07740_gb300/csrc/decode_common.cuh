@@ -22,12 +22,30 @@ using qc::exact_shape;
 #define QCLDPC_VN_VPT 3
 #endif
 #ifndef QCLDPC_VN_UNROLL
-#define QCLDPC_VN_UNROLL 6
+#define QCLDPC_VN_UNROLL 3
 #endif
+#ifndef QCLDPC_VN_VPT_MAX
+#define QCLDPC_VN_VPT_MAX 3
+#endif
+constexpr int kVnVptMax = QCLDPC_VN_VPT_MAX;
+static_assert(kVnVptMax >= 1 && kVnVptMax <= 3, "variable-pass nodes per thread: 1 to 3");
 constexpr int kThreads = 256;
 constexpr int kVnVpt = QCLDPC_VN_VPT;  // variable nodes per thread
 constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
+// Variable pass: each node's sum is kVnParts interleaved partial sums
+// (independent chains, added in a fixed order); the loop over a column's
+// circulants is unrolled kVnUnroll steps of kVnParts circulants
+// (kVnUnrollStaged when the column lists are staged in shared memory).
+#ifndef QCLDPC_VN_PARTS
+#define QCLDPC_VN_PARTS 2
+#endif
+constexpr int kVnParts = QCLDPC_VN_PARTS;
+#ifndef QCLDPC_VN_UNROLL_STAGED
+#define QCLDPC_VN_UNROLL_STAGED 6
+#endif
+constexpr int kVnUnrollStaged = QCLDPC_VN_UNROLL_STAGED;
 constexpr int kColChunk = 128;  // heavy-column circulants staged per chunk by the variable pass
+static_assert(kColChunk % kVnParts == 0, "column chunks must keep each circulant's part");
 constexpr int kCtrlThreads = 256;
 constexpr int kGraphCacheSize = 8;
 // Check-node pass with bulk-copy staging: one block stages up to kTile

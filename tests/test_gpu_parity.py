@@ -351,6 +351,31 @@ def test_full_size_batch_parity_few_iterations():
         assert_posteriors_close(post[f], ref, f"frame {f}")
 
 
+def test_results_do_not_depend_on_the_batch():
+    """A frame decodes to the same bits alone and in a batch, although the
+    launch shapes differ (variable pass: 1 node per thread alone, 3 in a
+    16-frame batch): a check's arithmetic does not depend on its tile, and
+    the variable pass adds each node's partial sums in a fixed order.
+    n = 10^6: one frame alone against the same frame first and last in a
+    16-frame batch."""
+    F, iters = 16, 6
+    d = synth.rate002_code(20000)
+    fr = make_frames(d, 0.029, 1)
+    code = q.create_code_from(d)
+    n = fr.code.n
+    x = np.concatenate([fr.x32] + [fr.x32 * 0.5] * (F - 2) + [fr.x32])
+    m = np.concatenate([fr.m32] * F)
+    syn = np.concatenate([fr.syn] * F)
+    llr = torch.empty(F * n, dtype=torch.float32, device="cuda")
+    q.qcldpc_llr_8d(dev(x.reshape(-1)), dev(m.reshape(-1)), F * n, 0.029, llr)
+    batch = decode_soft(code, llr, syn, F, iters, et_start=iters + 1)
+    alone = decode_soft(code, llr[:n].clone(), fr.syn, 1, iters, et_start=iters + 1)
+    for f in (0, F - 1):
+        np.testing.assert_array_equal(batch[3][f], alone[3][0], f"frame {f} posteriors")
+        np.testing.assert_array_equal(batch[0][f], alone[0][0], f"frame {f} keys")
+        assert (batch[1][f], batch[2][f]) == (alone[1][0], alone[2][0])
+
+
 def test_full_size_converged_frames_satisfy_the_syndrome():
     """At SNR 0.15 n=10^6 frames converge within a few iterations: the hard
     decisions of every converged frame satisfy H C = s (checked by the
