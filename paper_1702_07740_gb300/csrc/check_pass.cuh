@@ -23,7 +23,7 @@ enum CnMode { kFirst = 0, kSteady = 1, kSteadyTest = 2, kTestOnly = 3 };
 // predication; used for shapes the exact instantiations do not cover.
 template <int MAXD, typename M>
 __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, int f, int r, int t,
-                                               int mode, int i0, int vpt) {
+                                               int mode, int i0, int vpt, int stride) {
     const bool update = mode != kTestOnly;
     const bool read_msg = mode == kSteady || mode == kSteadyTest;
     const bool test = mode == kSteadyTest || mode == kTestOnly;
@@ -41,7 +41,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
     const uint32_t *syn = W.syn + (size_t)f * W.words_m;
     bool bad = false;
     for (int u = 0; u < vpt; u++) {
-        const int i = i0 + u * (int)blockDim.x;
+        const int i = i0 + u * stride;
         const bool valid = i < Z;
         const int cidx = r * Z + i;
         const uint32_t sbit = __ldg(syn + min(cidx >> 5, (int)W.words_m - 1)) << (31 - (cidx & 31));
@@ -195,9 +195,17 @@ __device__ __noinline__ void soft_deg1(const Table &T, const Work &W, int f, int
         W.llr[(size_t)f * W.n + (size_t)re.col * Z + vo] + kLn2 * __uint_as_float(fbits(mag) ^ sk);
 }
 
-template <int NH, int ND, int MODE, typename M, int NT>
-__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int rp, int t,
-                                        const qc::RowDesc *dp, unsigned char *smem) {
+// The arithmetic of one tile of checks i0 .. i0 + nt * kTmaVpt - 1 of base
+// row r, frame f, from operand rows staged in shared memory (s_off: each
+// row's first element, in units of its element type, from `stage`). ob: the
+// row entries' output offsets. sy0 / b0: the syndrome word holding check
+// r Z + i0 and that check's bit in it (a global pointer, or a staged copy
+// when SYN_SMEM). wait() runs after the syndrome loads and reports whether
+// the staged rows arrived. Thread tid < nt owns checks i0 + c nt + tid.
+template <int NH, int ND, int MODE, typename M, int NT, bool SYN_SMEM, typename Wait>
+__device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f, int r, int rp, int t,
+                                           int i0, const int *ob, const int *s_off, const float *stage,
+                                           const uint32_t *sy0, int b0, Wait wait) {
     constexpr int D = NH + ND;
     constexpr int NHa = NH > 0 ? NH : 1;
     constexpr int NDa = ND > 0 ? ND : 1;
@@ -205,72 +213,11 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
     constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
     constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
     const int Z = T.Z, ZW = W.ZW;
-    int oa[qc::kDescEnts], ob[qc::kDescEnts];
-    load_offsets(dp, oa, ob);
     const int nt = NT ? NT : (int)blockDim.x;  // threads: a multiple of 32, at most kCnThreads
-    const int ws = nt >> 5;            // decision words per check slot
-    const int tile = nt * kTmaVpt;     // checks per block
-    const int i0 = blockIdx.x * tile;
+    const int ws = nt >> 5;                    // decision words per check slot
     const int tid = threadIdx.x;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *s_off = reinterpret_cast<int *>(smem + 16);  // per staged row: start of its data
-    float *stage = reinterpret_cast<float *>(smem + kSmemHeader);
     const size_t bstride = (size_t)T.n_d1 * ZW;
-    // messages of iteration t-1 (read) and t (written); one buffer when flooding
-    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
     M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
-
-    // Thread 0: arm the barrier, publish each staged row's read offset
-    // (row slot * (tile + 4) + 16-byte remainder), then issue the copies.
-    // Staged rows: NH posteriors, NH old messages (kReadMsg), ND psi values
-    // (kUpdate), then ND decision-word rows of tile / 32 + 4 words (kTest).
-    if (tid == 0) {
-        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
-        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
-        const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
-        mbar_init(bar, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const void *src[2 * NHa + 2 * NDa];
-        uint32_t nb[2 * NHa + 2 * NDa];
-        int slot_start[2 * NHa + 2 * NDa];
-        int ncopy = 0, pos = 0;
-        uint32_t total = 0;
-        // Each staged row takes row_slots 4-byte slots; s_off holds the row's
-        // first element in units of its own element size.
-        auto add = [&](const void *p, uint32_t count, int esize, int row_slots) {
-            int rem;
-            nb[ncopy] = stage_bytes(p, count, esize, &rem);
-            src[ncopy] = reinterpret_cast<const char *>(p) - esize * rem;
-            slot_start[ncopy] = pos;
-            s_off[ncopy] = pos * (4 / esize) + rem;
-            total += nb[ncopy];
-            pos += row_slots;
-            ncopy++;
-        };
-        // only the tile's checks below Z are copied (the last tile of a row
-        // would otherwise pull in its neighbour's data)
-        const uint32_t nv = (uint32_t)min(tile, Z - i0);
-        const int row_slots = tile + 4, word_slots = tile / 32 + 4;
-#pragma unroll
-        for (int k = 0; k < NH; k++) add(L + oa[k] + i0, nv, 4, row_slots);
-        if (kReadMsg) {
-#pragma unroll
-            for (int k = 0; k < NH; k++)
-                add(msg_rd + ob[k] + i0, nv, (int)sizeof(M), row_slots);
-        }
-        if (kUpdate) {
-#pragma unroll
-            for (int k = 0; k < ND; k++) add(phiq + oa[NH + k] + i0, nv, 4, row_slots);
-        }
-        if (kTest) {
-#pragma unroll
-            for (int k = 0; k < ND; k++)
-                add(bprev + ob[NH + k] + (i0 >> 5), (nv + 31) / 32, 4, word_slots);
-        }
-        mbar_expect_tx(bar, total);
-        for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
-    }
-    __syncthreads();  // barrier initialised, offsets published
 
     // Per-row pointers for this thread's first check; check c sits at
     // + c * nt elements (or + c * ws words).
@@ -306,19 +253,19 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
             else oB[k - NH] = bcur + ob[k] + (i0 >> 5) + (tid >> 5);
         }
     }
-    const int c0 = r * Z + i0 + tid;
-    const uint32_t *sy = W.syn + (size_t)f * W.words_m + (c0 >> 5);
-    const int ssh = 31 - (c0 & 31);
+    // syndrome words of the owned checks (check c of this thread sits c * ws
+    // words after the first), loaded while the copies are in flight
+    const int sb = b0 + tid;
+    const uint32_t *sy = sy0 + (sb >> 5);
+    const int ssh = 31 - (sb & 31);
     const int dsh = 31 - (tid & 31);
     const bool lane0 = (tid & 31) == 0;
-
-    // syndrome words of the owned checks, loaded while the copies are in flight
     uint32_t sw[kTmaVpt];
 #pragma unroll
     for (int c = 0; c < kTmaVpt; c++)
-        sw[c] = i0 + c * nt + tid < Z ? (__ldg(sy + c * ws) << ssh) : 0u;
+        sw[c] = i0 + c * nt + tid < Z ? ((SYN_SMEM ? sy[c * ws] : __ldg(sy + c * ws)) << ssh) : 0u;
 
-    const bool staged = stage_wait(bar, W);
+    const bool staged = wait();
     bool bad = false;
     if (staged) {
       if constexpr (QCLDPC_CN_PAIR && kTmaVpt % 2 == 0) {
@@ -384,15 +331,14 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
                     const float2 s2 = k == 0       ? suf[1]
                                       : k == D - 1 ? pre[D - 2]
                                                    : __fadd2_rn(pre[k - 1], suf[k + 1]);
-                    const float2 ex = make_float2(fmaxf(s2.x, W.xmin), fmaxf(s2.y, W.xmin));
                     const uint32_t ska = (sta ^ sga[k]) & kSign, skb = (stb ^ sgb[k]) & kSign;
                     if (k < NH) {
-                        const float2 mag = psi2(ex);
-                        if (va) oM[k][c * nt] =
-                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.x, W.clip)) ^ ska), W);
-                        if (vb) oM[k][(c + 1) * nt] =
-                            Codec<M>::enc(__uint_as_float(fbits(fminf(mag.y, W.clip)) ^ skb), W);
+                        // min(psi(max(s, xmin)), clip) = psi(max(s, xmin_h))
+                        const float2 mag = psi2(make_float2(fmaxf(s2.x, W.xmin_h), fmaxf(s2.y, W.xmin_h)));
+                        if (va) oM[k][c * nt] = Codec<M>::enc(__uint_as_float(fbits(mag.x) ^ ska), W);
+                        if (vb) oM[k][(c + 1) * nt] = Codec<M>::enc(__uint_as_float(fbits(mag.y) ^ skb), W);
                     } else {
+                        const float2 ex = make_float2(fmaxf(s2.x, W.xmin), fmaxf(s2.y, W.xmin));
                         const uint32_t da = ex.x < phi[k].x ? ska : (sga[k] & kSign);
                         const uint32_t db = ex.y < phi[k].y ? skb : (sgb[k] & kSign);
                         const uint32_t wa = __ballot_sync(0xffffffffu, va && da != 0);
@@ -451,12 +397,13 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
                 for (int k = D - 1; k >= 0; k--) suf[k] = suf[k + 1] + phi[k];
 #pragma unroll
                 for (int k = 0; k < D; k++) {
-                    const float ex = fmaxf(pre[k] + suf[k + 1], W.xmin);
+                    const float s1 = pre[k] + suf[k + 1];
                     const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
                     if (k < NH) {
-                        const float mag = fminf(psi_f(ex), W.clip);
+                        const float mag = psi_f(fmaxf(s1, W.xmin_h));
                         if (valid) oM[k][c * nt] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
                     } else {
+                        const float ex = fmaxf(s1, W.xmin);
                         const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
                         const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
                         if (lane0 && valid) oB[k - NH][c * ws] = word;
@@ -467,6 +414,88 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
         }
       }
     }
+    return bad;
+}
+
+template <int NH, int ND, int MODE, typename M, int NT>
+__device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, int r, int rp, int t,
+                                        const qc::RowDesc *dp, unsigned char *smem) {
+    constexpr int NHa = NH > 0 ? NH : 1;
+    constexpr int NDa = ND > 0 ? ND : 1;
+    constexpr bool kUpdate = MODE != kTestOnly;
+    constexpr bool kReadMsg = MODE == kSteady || MODE == kSteadyTest;
+    constexpr bool kTest = MODE == kSteadyTest || MODE == kTestOnly;
+    const int Z = T.Z, ZW = W.ZW;
+    int oa[qc::kDescEnts], ob[qc::kDescEnts];
+    load_offsets(dp, oa, ob);
+    const int nt = NT ? NT : (int)blockDim.x;  // threads: a multiple of 32, at most kCnThreads
+    const int tile = nt * kTmaVpt;     // checks per block
+    const int i0 = blockIdx.x * tile;
+    const int tid = threadIdx.x;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *s_off = reinterpret_cast<int *>(smem + 16);  // per staged row: start of its data
+    float *stage = reinterpret_cast<float *>(smem + kSmemHeader);
+    const size_t bstride = (size_t)T.n_d1 * ZW;
+    // messages of iteration t-1 (read); layered decoding writes those of t
+    // to the other buffer
+    const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
+
+    // Thread 0: arm the barrier, publish each staged row's read offset
+    // (row slot * (tile + 4) + 16-byte remainder), then issue the copies.
+    // Staged rows: NH posteriors, NH old messages (kReadMsg), ND psi values
+    // (kUpdate), then ND decision-word rows of tile / 32 + 4 words (kTest).
+    if (tid == 0) {
+        const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
+        const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
+        const uint32_t *bprev = W.bits + ((size_t)((t - 1) & 1) * W.n_frames + f) * bstride;
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        const void *src[2 * NHa + 2 * NDa];
+        uint32_t nb[2 * NHa + 2 * NDa];
+        int slot_start[2 * NHa + 2 * NDa];
+        int ncopy = 0, pos = 0;
+        uint32_t total = 0;
+        // Each staged row takes row_slots 4-byte slots; s_off holds the row's
+        // first element in units of its own element size.
+        auto add = [&](const void *p, uint32_t count, int esize, int row_slots) {
+            int rem;
+            nb[ncopy] = stage_bytes(p, count, esize, &rem);
+            src[ncopy] = reinterpret_cast<const char *>(p) - esize * rem;
+            slot_start[ncopy] = pos;
+            s_off[ncopy] = pos * (4 / esize) + rem;
+            total += nb[ncopy];
+            pos += row_slots;
+            ncopy++;
+        };
+        // only the tile's checks below Z are copied (the last tile of a row
+        // would otherwise pull in its neighbour's data)
+        const uint32_t nv = (uint32_t)min(tile, Z - i0);
+        const int row_slots = tile + 4, word_slots = tile / 32 + 4;
+#pragma unroll
+        for (int k = 0; k < NH; k++) add(L + oa[k] + i0, nv, 4, row_slots);
+        if (kReadMsg) {
+#pragma unroll
+            for (int k = 0; k < NH; k++)
+                add(msg_rd + ob[k] + i0, nv, (int)sizeof(M), row_slots);
+        }
+        if (kUpdate) {
+#pragma unroll
+            for (int k = 0; k < ND; k++) add(phiq + oa[NH + k] + i0, nv, 4, row_slots);
+        }
+        if (kTest) {
+#pragma unroll
+            for (int k = 0; k < ND; k++)
+                add(bprev + ob[NH + k] + (i0 >> 5), (nv + 31) / 32, 4, word_slots);
+        }
+        mbar_expect_tx(bar, total);
+        for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
+    }
+    __syncthreads();  // barrier initialised, offsets published
+
+    const int cb0 = r * Z + i0;
+    const bool bad = cn_compute<NH, ND, MODE, M, NT, false>(
+        T, W, f, r, rp, t, i0, ob, s_off, stage, W.syn + (size_t)f * W.words_m + (cb0 >> 5), cb0 & 31,
+        [&] { return stage_wait(bar, W); });
     __syncthreads();
     if (tid == 0) mbar_inval(bar);
     return bad;
@@ -526,7 +555,7 @@ __global__ void __launch_bounds__(kCnThreads, NT ? QCLDPC_CN_TMA_MINBLOCKS : QCL
         }
     } else {
         bad = cn_row_generic<MAXD, M>(T, W, f, r, t, mode, blockIdx.x * blockDim.x * kTmaVpt + threadIdx.x,
-                                      kTmaVpt);
+                                      kTmaVpt, (int)blockDim.x);
     }
     if (mode == kSteadyTest || mode == kTestOnly) {
         if (__syncthreads_or(bad) && threadIdx.x == 0) W.fail[f] = 1;

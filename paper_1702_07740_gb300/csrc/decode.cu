@@ -488,6 +488,19 @@ void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
     *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
+// Floor of a heavy check output's exclusive psi sum (base-2 units). psi is
+// decreasing and its own inverse, so clipping the output, min(psi(max(s,
+// xmin)), clip), equals psi(max(s, xmin, psi(clip))). With the default clip
+// psi(clip) is below xmin and the floor is xmin itself; otherwise it sits a
+// hair above psi(clip), so that the FP32 psi of it stays at or below clip.
+float heavy_out_floor(float clip2, float xmin2) {
+    if (!(clip2 < INFINITY)) return xmin2;
+    const double t = std::exp2(-(double)clip2);
+    const double psi_clip = std::log2((1.0 + t) / (1.0 - t));
+    if (psi_clip * (1.0 + 1e-4) < (double)xmin2) return xmin2;
+    return (float)(std::max((double)xmin2, psi_clip) * (1.0 + 1e-4));
+}
+
 // Launch of the check-node pass for a code: kernel, grid and dynamic shared
 // memory (the staged variant needs the code's widest exact-shape row).
 struct CnLaunch {
@@ -779,6 +792,7 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.ZW = (T.Z + 31) / 32;
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;  // base-2 units
     w.xmin = p.phi_floor * kLog2e;
+    w.xmin_h = heavy_out_floor(w.clip, w.xmin);
     w.fmt = p.msg_format;
     if (w.fmt == 2) {
         // int8 quantum: msg_step natural-LLR units, default clip / 127
@@ -1271,6 +1285,7 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     w.ZW = (code->tab.Z + 31) / 32;
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;
     w.xmin = p.phi_floor * kLog2e;
+    w.xmin_h = heavy_out_floor(w.clip, w.xmin);
     w.fmt = p.msg_format;
     if (w.fmt == 2) {
         const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;

@@ -118,6 +118,8 @@ struct Work {
     int64_t n, words_m, words_k;
     int32_t n_frames, max_iter, et_start, soft, ZW, fmt;
     float clip, xmin;      // base-2 units
+    float xmin_h;          // floor of a heavy output's exclusive sum: max(xmin, psi(clip)),
+                           // so that psi of it needs no clip (psi decreases, psi(psi(y)) = y)
     float qstep, qinv;     // int8 message quantum and its inverse (base-2 units)
     int64_t msg_buf;       // layered: elements per message buffer; 0 for flooding
     int32_t layered;       // schedule: 0 flooding, 1 layered

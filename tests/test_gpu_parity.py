@@ -257,6 +257,23 @@ def test_decode_zero_iterations_returns_channel_decisions():
         assert_posteriors_close(post[f], ref)
 
 
+@pytest.mark.parametrize("clip", [2.0, 5.0])
+def test_binding_clip_matches_oracle(clip):
+    """A clip low enough to bind on check outputs (psi(clip) above the floor
+    of the psi sums): the GPU folds the output clip into that floor, the
+    oracle clips each message; posteriors agree to the usual tolerance."""
+    fr = make_frames(synth.rate002_code(512), 0.3, 2)
+    code = q.create_code_from(fr.code_dict)
+    iters = 20
+    keys, conv, its, post = decode_soft(code, gpu_llr(fr), fr.syn, fr.F, iters, et_start=iters + 1,
+                                        clip=clip)
+    for f in range(fr.F):
+        ref, _, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], iters, et_start=iters + 1,
+                                       clip=clip)
+        assert_posteriors_close(post[f], ref, f"clip {clip} frame {f}")
+        assert its[f] == it and conv[f] == int(cv)
+
+
 @pytest.mark.parametrize("Z", [700, 1500, 2000, 2052])
 def test_check_block_widths_match_oracle(Z):
     """The check pass sizes its blocks to Z: 1024-check tiles when those fill
