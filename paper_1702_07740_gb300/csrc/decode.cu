@@ -176,40 +176,46 @@ __global__ void __launch_bounds__(kCtrlThreads) ctrl_kernel(const __grid_constan
 // Grid (tile, heavy column, frame). Lanes past the end of the column read
 // message padding (never stored); the channel LLRs, the caller's buffer, are
 // read only in range.
-// Each thread keeps kVnParts independent partial sums per node, part p over
-// the column's circulants p, p + kVnParts, ... in order (part 0 starts from
-// Q_v), and adds them in part order at the end: the chains hide the load
-// latency of small batches, and the order is fixed, so a frame's result does
-// not depend on the launch shape or the batch it is decoded in.
-template <typename M, int VPT>
+// A node's sum is kVnParts independent partial sums, part p over the
+// column's circulants p, p + kVnParts, ... in order (part 0 starts from
+// Q_v), added in part order at the end. With S = 1 a thread keeps every part
+// of its nodes (independent chains hide load latency); with S = kVnParts the
+// block's threads form S groups over the same kThreads / S nodes, group g
+// computes part g, and group 0 adds the others' parts from shared memory in
+// the same order. Both forms give the same bits, so the launch picks S by
+// batch size and a frame's result never depends on its batch.
+template <typename M, int VPT, int S>
 __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Table T,
                                                       const __grid_constant__ Work W,
                                                       const __grid_constant__ qc::ColsInline C) {
-    constexpr int P = kVnParts;
+    constexpr int P = kVnParts, G = kThreads / S, NP = P / S;  // parts held per thread
+    static_assert(S == 1 || S == P, "a thread holds one part or all of them");
     pdl_wait();  // the control step's flags are complete and visible
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;
     const int Z = T.Z;
     const int hc = blockIdx.y;
-    const int j0 = blockIdx.x * (kThreads * VPT) + threadIdx.x;
+    const int g = S == 1 ? 0 : (int)threadIdx.x / G;
+    const int lt = (int)threadIdx.x - g * G;
+    const int j0 = blockIdx.x * (G * VPT) + lt;
     const M *__restrict__ msg = static_cast<const M *>(W.msg) + (size_t)f * T.n_h * Z;
     const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
     float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
-    float acc[VPT][P];
+    float acc[VPT][NP];
 #pragma unroll
     for (int u = 0; u < VPT; u++) {
-        const int j = j0 + u * kThreads;
+        const int j = j0 + u * G;
 #pragma unroll
-        for (int p = 0; p < P; p++) acc[u][p] = (p == 0 && j < Z) ? __ldg(q + j) * kLog2e : 0.0f;
+        for (int i = 0; i < NP; i++) acc[u][i] = (g == 0 && i == 0 && j < Z) ? __ldg(q + j) * kLog2e : 0.0f;
     }
-    // add circulant (shift, id) to part p
-    auto add = [&](int shift, int id, int p) {
+    // add circulant (shift, id) to the thread's part slot i
+    auto add = [&](int shift, int id, int i) {
         const M *__restrict__ mk = msg + id * Z;
 #pragma unroll
         for (int u = 0; u < VPT; u++) {
-            int idx = j0 + u * kThreads - shift;
+            int idx = j0 + u * G - shift;
             if (idx < 0) idx += Z;
-            acc[u][p] += Codec<M>::dec(mk[idx], W);
+            acc[u][i] += Codec<M>::dec(mk[idx], W);
         }
     };
     if (C.ok) {
@@ -220,16 +226,16 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
 #pragma unroll kVnUnroll
         for (; k + P <= ce; k += P) {
 #pragma unroll
-            for (int p = 0; p < P; p++) {
-                const qc::ColEnt e = C.cols[k + p];
-                add(e.shift, e.id, p);
+            for (int i = 0; i < NP; i++) {
+                const qc::ColEnt e = C.cols[k + g + i * S];
+                add(e.shift, e.id, i);
             }
         }
 #pragma unroll
-        for (int p = 0; p < P - 1; p++) {
-            if (k + p < ce) {
-                const qc::ColEnt e = C.cols[k + p];
-                add(e.shift, e.id, p);
+        for (int i = 0; i < NP; i++) {
+            if (k + g + i * S < ce) {
+                const qc::ColEnt e = C.cols[k + g + i * S];
+                add(e.shift, e.id, i);
             }
         }
     } else {
@@ -247,27 +253,48 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
 #pragma unroll kVnUnrollStaged
         for (; kk + P <= cnt; kk += P) {
 #pragma unroll
-            for (int p = 0; p < P; p++) {
-                const int2 e = s_cols[kk + p];
-                add(e.x, e.y, p);
+            for (int i = 0; i < NP; i++) {
+                const int2 e = s_cols[kk + g + i * S];
+                add(e.x, e.y, i);
             }
         }
 #pragma unroll
-        for (int p = 0; p < P - 1; p++) {
-            if (kk + p < cnt) {
-                const int2 e = s_cols[kk + p];
-                add(e.x, e.y, p);
+        for (int i = 0; i < NP; i++) {
+            if (kk + g + i * S < cnt) {
+                const int2 e = s_cols[kk + g + i * S];
+                add(e.x, e.y, i);
             }
         }
     }
+    }
+    float tot[VPT];
+    if constexpr (S == 1) {
+#pragma unroll
+        for (int u = 0; u < VPT; u++) {
+            tot[u] = acc[u][0];
+#pragma unroll
+            for (int p = 1; p < P; p++) tot[u] += acc[u][p];
+        }
+    } else {
+        __shared__ float s_part[P - 1][G * VPT];
+        if (g > 0) {
+#pragma unroll
+            for (int u = 0; u < VPT; u++) s_part[g - 1][u * G + lt] = acc[u][0];
+        }
+        __syncthreads();
+        if (g > 0) return;
+#pragma unroll
+        for (int u = 0; u < VPT; u++) {
+            tot[u] = acc[u][0];
+#pragma unroll
+            for (int p = 1; p < P; p++) tot[u] += s_part[p - 1][u * G + lt];
+        }
     }
 #pragma unroll
     for (int u = 0; u < VPT; u++) {
-        const int j = j0 + u * kThreads;
+        const int j = j0 + u * G;
         if (j < Z) {
-            float lvj = acc[u][0];
-#pragma unroll
-            for (int p = 1; p < P; p++) lvj += acc[u][p];
+            float lvj = tot[u];
             lvj += 0.0f;  // -0 -> +0: sgn(0) = +1 everywhere
             L[j] = lvj;
             L[j + Z] = lvj;
@@ -427,31 +454,42 @@ struct VnLaunch {
 };
 
 template <typename M>
-void *vn_kernel_vpt(int vpt) {
-    if (vpt == 3) return (void *)vn_kernel<M, 3>;
-    if (vpt == 2) return (void *)vn_kernel<M, 2>;
-    return (void *)vn_kernel<M, 1>;
+void *vn_kernel_for(int vpt, int split) {
+    if (split == 1) {
+        if (vpt == 3) return (void *)vn_kernel<M, 3, 1>;
+        if (vpt == 2) return (void *)vn_kernel<M, 2, 1>;
+        return (void *)vn_kernel<M, 1, 1>;
+    }
+    if (vpt == 3) return (void *)vn_kernel<M, 3, kVnParts>;
+    if (vpt == 2) return (void *)vn_kernel<M, 2, kVnParts>;
+    return (void *)vn_kernel<M, 1, kVnParts>;
 }
 
 int sm_count();
 
-// Variable-pass launch: the nodes per thread (VPT) is the largest of
-// kVnVptMax ... 1 that still leaves four blocks per SM.
+// Variable-pass launch: batches whose heavy nodes fill fewer than
+// kVnSplitBlocks 256-node blocks per SM give each part of a node's sum its
+// own thread group (same bits, kVnParts times the threads); then the nodes
+// per thread (VPT) is the largest of kVnVptMax ... 1 that still leaves four
+// blocks per SM.
 VnLaunch vn_launch(const Table &T, int F, int fmt) {
     const int hc = std::max(T.n_hcols, 1);
-    const long long want = 4LL * sm_count();
+    const long long sms = sm_count();
+    const long long blocks1 = (long long)F * hc * ((T.Z + kThreads - 1) / kThreads);
+    const int split = (kVnParts > 1 && blocks1 < kVnSplitBlocks * sms) ? kVnParts : 1;
+    const int G = kThreads / split;
     int vpt = 1;
     for (int v = kVnVptMax; v >= 1; v--) {
-        const long long blocks = (long long)F * hc * ((T.Z + kThreads * v - 1) / (kThreads * v));
-        if (blocks >= want || v == 1) {
+        const long long blocks = (long long)F * hc * ((T.Z + G * v - 1) / (G * v));
+        if (blocks >= 4 * sms || v == 1) {
             vpt = v;
             break;
         }
     }
     VnLaunch l;
-    l.grid = dim3((unsigned)((T.Z + kThreads * vpt - 1) / (kThreads * vpt)), (unsigned)hc, (unsigned)F);
-    l.func = fmt == 1 ? vn_kernel_vpt<__half>(vpt) : fmt == 2 ? vn_kernel_vpt<int8_t>(vpt)
-                                                             : vn_kernel_vpt<float>(vpt);
+    l.grid = dim3((unsigned)((T.Z + G * vpt - 1) / (G * vpt)), (unsigned)hc, (unsigned)F);
+    l.func = fmt == 1 ? vn_kernel_for<__half>(vpt, split) : fmt == 2 ? vn_kernel_for<int8_t>(vpt, split)
+                                                                    : vn_kernel_for<float>(vpt, split);
     return l;
 }
 

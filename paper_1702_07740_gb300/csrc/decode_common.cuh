@@ -40,6 +40,13 @@ constexpr int kVnUnroll = QCLDPC_VN_UNROLL;
 #define QCLDPC_VN_PARTS 2
 #endif
 constexpr int kVnParts = QCLDPC_VN_PARTS;
+static_assert(kThreads % (32 * kVnParts) == 0, "variable-pass part groups must be whole warps");
+// Batches below this many 256-node variable-pass blocks per SM split each
+// node's parts over thread groups.
+#ifndef QCLDPC_VN_SPLIT_BLOCKS
+#define QCLDPC_VN_SPLIT_BLOCKS 8
+#endif
+constexpr int kVnSplitBlocks = QCLDPC_VN_SPLIT_BLOCKS;
 #ifndef QCLDPC_VN_UNROLL_STAGED
 #define QCLDPC_VN_UNROLL_STAGED 6
 #endif
