@@ -181,6 +181,15 @@ typedef struct qcldpc_params {
     int32_t layers;      /* layered schedule: number of row groups, 1..mb;
                             0 (default) = one group per base row. Ignored by
                             flooding. layers = 1 computes what flooding does */
+    /* Launch shapes; 0 (default) lets the library choose. None of them
+       changes a result bit (qcldpc_autotune_shapes picks them by time). */
+    int32_t cn_threads;  /* threads per check-pass block: a multiple of 32,
+                            32..256; a block evaluates 4 checks per thread of
+                            one base row */
+    int32_t vn_nodes;    /* variable pass: heavy nodes per thread, 1..3 */
+    int32_t vn_split;    /* variable pass: 1 = a thread adds both partial sums
+                            of its nodes, 2 = two thread groups, one per
+                            partial sum (added in the same order) */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);
@@ -307,6 +316,27 @@ int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev, const uint32_
                     uint32_t *key_bits_dev, int32_t *converged_dev, int32_t *iters_dev,
                     void *workspace_dev, size_t workspace_bytes, int reps,
                     qcldpc_params *best, float *times_ms, qcldpc_stream_t stream);
+
+/*
+ * Launch-shape autotuner; the paper has no counterpart. On the state a
+ * previous flooding qcldpc_decode / qcldpc_decode_soft call with the same
+ * code, n_frames and workspace left behind, replays the check-node pass with
+ * blocks of 32, 64, ..., 256 threads, and the variable-node pass with (nodes
+ * per thread, vn_split) = (1,1), (2,1), (3,1), (1,2), (2,2), (3,2), each
+ * `reps` times after one warm-up launch (CUDA events on `stream`).
+ *   p        options the shapes are tuned for (NULL = defaults)
+ *   best     out: *p with cn_threads, vn_nodes and vn_split set to the
+ *            fastest candidates
+ *   cn_ms    out (may be NULL): 8 mean check-pass times, ms, in that order
+ *   vn_ms    out (may be NULL): 6 mean variable-pass times, ms
+ * Every shape computes the same bits. Overwrites the decoder state in the
+ * workspace as qcldpc_time_passes does; blocks the calling thread.
+ * Errors: QCLDPC_E_INVAL (no matching previous flooding decode), _NOMEM,
+ * _CUDA.
+ */
+int qcldpc_autotune_shapes(const qcldpc_code *code, int n_frames, void *workspace_dev,
+                           size_t workspace_bytes, int reps, const qcldpc_params *p,
+                           qcldpc_params *best, float *cn_ms, float *vn_ms, qcldpc_stream_t stream);
 
 /*
  * Measurement helper; the paper has no counterpart. Replays the check-node

@@ -162,6 +162,9 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->launch_mode = 0;
     p->msg_step = 0.0f;
     p->layers = 0;
+    p->cn_threads = 0;
+    p->vn_nodes = 0;
+    p->vn_split = 0;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,

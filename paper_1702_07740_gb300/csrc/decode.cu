@@ -472,11 +472,13 @@ int sm_count();
 // own thread group (same bits, kVnParts times the threads); then the nodes
 // per thread (VPT) is the largest of kVnVptMax ... 1 that still leaves four
 // blocks per SM.
-VnLaunch vn_launch(const Table &T, int F, int fmt) {
+// vpt_set / split_set (non-zero) override the choice (qcldpc_params
+// vn_nodes / vn_split); every shape computes the same bits.
+VnLaunch vn_launch(const Table &T, int F, int fmt, int vpt_set = 0, int split_set = 0) {
     const int hc = std::max(T.n_hcols, 1);
     const long long sms = sm_count();
     const long long blocks1 = (long long)F * hc * ((T.Z + kThreads - 1) / kThreads);
-    const int split = (kVnParts > 1 && blocks1 < kVnSplitBlocks * sms) ? kVnParts : 1;
+    const int split = split_set ? split_set : (kVnParts > 1 && blocks1 < kVnSplitBlocks * sms) ? kVnParts : 1;
     const int G = kThreads / split;
     int vpt = 1;
     for (int v = kVnVptMax; v >= 1; v--) {
@@ -486,6 +488,7 @@ VnLaunch vn_launch(const Table &T, int F, int fmt) {
             break;
         }
     }
+    if (vpt_set) vpt = vpt_set;
     VnLaunch l;
     l.grid = dim3((unsigned)((T.Z + G * vpt - 1) / (G * vpt)), (unsigned)hc, (unsigned)F);
     l.func = fmt == 1 ? vn_kernel_for<__half>(vpt, split) : fmt == 2 ? vn_kernel_for<int8_t>(vpt, split)
@@ -526,6 +529,13 @@ void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
     *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
+// Launch-shape options: 0 (chosen by the library) or a supported value.
+bool shape_ok(const qcldpc_params &p) {
+    return (p.cn_threads == 0 || (p.cn_threads >= 32 && p.cn_threads <= kCnThreads && p.cn_threads % 32 == 0)) &&
+           (p.vn_nodes >= 0 && p.vn_nodes <= kVnVptMax) &&
+           (p.vn_split == 0 || p.vn_split == 1 || p.vn_split == kVnParts);
+}
+
 // Floor of a heavy check output's exclusive psi sum (base-2 units). psi is
 // decreasing and its own inverse, so clipping the output, min(psi(max(s,
 // xmin)), clip), equals psi(max(s, xmin, psi(clip))). With the default clip
@@ -559,10 +569,12 @@ int cn_threads(int Z) {
     return std::min(kCnThreads, 32 * ((per + 32 * kTmaVpt - 1) / (32 * kTmaVpt)));
 }
 
-CnLaunch cn_launch(const Table &T, int F, int fmt) {
+// nt_set (non-zero) overrides the block width (qcldpc_params cn_threads);
+// a check's arithmetic does not depend on it.
+CnLaunch cn_launch(const Table &T, int F, int fmt, int nt_set = 0) {
     CnLaunch c;
     {
-        const int nt = cn_threads(T.Z), tile = nt * kTmaVpt;
+        const int nt = nt_set ? nt_set : cn_threads(T.Z), tile = nt * kTmaVpt;
         // the code's widest exact-shape row (its staged rows and word rows)
         const size_t smem = kSmemHeader + (size_t)T.stage_rows_max * (tile + 4) * 4 +
                             (size_t)T.stage_words_max * (tile / 32 + 4) * 4;
@@ -642,7 +654,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
     void *args[] = {&tcopy, &wcopy};
     void *vn_args[] = {&tcopy, &wcopy, &ccopy};
     cudaGraphNode_t n_cn, n_ctrl, n_vn;
-    const CnLaunch cl = cn_launch(T, F, w0.fmt);
+    const CnLaunch cl = cn_launch(T, F, w0.fmt, w0.cn_nt);
     cudaError_t err;
     if (w0.layered) wcopy.pass = kPassTest;
     if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, cl.block, args,
@@ -654,7 +666,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
                           dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
         return err;
     if (!w0.layered) {
-        const VnLaunch vl = vn_launch(T, F, w0.fmt);
+        const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
         return add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0,
                           true);
     }
@@ -724,7 +736,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
     const int F = w.n_frames;
     const int blocks = sm_count() * 4;
     init_kernel<<<blocks, kThreads, 0, stream>>>(T, w);
-    const CnLaunch cl = cn_launch(T, F, w.fmt);
+    const CnLaunch cl = cn_launch(T, F, w.fmt, w.cn_nt);
     Table tcopy = T;
     Work wcopy = w;
     if (w.layered) wcopy.pass = kPassTest;
@@ -738,7 +750,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         if (t <= w.max_iter && !w.layered) {
             qc::ColsInline ccopy = code->cols_in;
             void *vn_args[] = {&tcopy, &wcopy, &ccopy};
-            const VnLaunch vl = vn_launch(T, F, w.fmt);
+            const VnLaunch vl = vn_launch(T, F, w.fmt, w.vn_vpt, w.vn_split);
             err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
         }
         for (int g = 0; t <= w.max_iter && w.layered && g < w.ngroups && err == cudaSuccess; g++) {
@@ -779,10 +791,10 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
     if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
         p.msg_format > 2 || !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1) ||
-        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)))
+        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)) || !shape_ok(p))
         return fail(QCLDPC_E_INVAL,
                     "decode: unsupported option (phi_floor > 0, schedule 0..1, layers 0..mb, "
-                    "msg_format 0..2, msg_step >= 0)");
+                    "msg_format 0..2, msg_step >= 0, launch shapes)");
     if (soft && p.soft_output != 1)
         return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
     if (F == 0) return QCLDPC_OK;
@@ -831,6 +843,9 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;  // base-2 units
     w.xmin = p.phi_floor * kLog2e;
     w.xmin_h = heavy_out_floor(w.clip, w.xmin);
+    w.cn_nt = p.cn_threads;
+    w.vn_vpt = p.vn_nodes;
+    w.vn_split = p.vn_split;
     w.fmt = p.msg_format;
     if (w.fmt == 2) {
         // int8 quantum: msg_step natural-LLR units, default clip / 127
@@ -986,6 +1001,82 @@ extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,
     return QCLDPC_OK;
 }
 
+// Launch-shape candidates of qcldpc_autotune_shapes, in the order of its
+// timing arrays: check blocks of 32, 64, ..., 256 threads; variable pass
+// (nodes per thread, part groups) = (1,1), (2,1), (3,1), (1,P), (2,P), (3,P).
+extern "C" int qcldpc_autotune_shapes(const qcldpc_code *code_c, int n_frames, void *workspace_dev,
+                                      size_t workspace_bytes, int reps, const qcldpc_params *p,
+                                      qcldpc_params *best, float *cn_ms, float *vn_ms,
+                                      qcldpc_stream_t stream_) {
+    using namespace qc;
+    qcldpc_code *code = const_cast<qcldpc_code *>(code_c);
+    if (!code || !workspace_dev || !best || reps < 1 || n_frames < 1 || n_frames > 65535)
+        return fail(QCLDPC_E_INVAL, "autotune_shapes: bad argument");
+    cudaStream_t stream = (cudaStream_t)stream_;
+    qcldpc_params base;
+    if (p) base = *p;
+    else qcldpc_params_init(&base);
+    std::lock_guard<std::mutex> lock(code->mu);
+    if (code->last_ws != workspace_dev || code->last_frames != n_frames)
+        return fail(QCLDPC_E_INVAL, "autotune_shapes: no decode ran on this workspace with this frame count");
+    Work w;
+    std::memcpy(&w, code->last_work, sizeof(w));
+    if (w.layered) return fail(QCLDPC_E_INVAL, "autotune_shapes: the last decode was layered (flooding only)");
+    const Layout lo = layout_of(code->tab, n_frames, code->last_soft != 0, w.fmt);
+    if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "autotune_shapes: workspace too small");
+    if (w.max_iter < 2) w.max_iter = 2;  // replays run as iteration 2: a full update
+    const Table &T = code->tab;
+    Table tcopy = T;
+    qc::ColsInline ccopy = code->cols_in;
+    void *args[] = {&tcopy, &w};
+    void *vn_args[] = {&tcopy, &w, &ccopy};
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err != cudaSuccess) return cuda_fail(err, "autotune_shapes: cudaEventCreate");
+    if ((err = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(err, "autotune_shapes: cudaEventCreate");
+    }
+    replay_prep_kernel<<<1, 256, 0, stream>>>(w);
+    // mean time of `reps` launches after one warm-up launch
+    auto time = [&](const void *func, dim3 grid, dim3 block, void **a, size_t smem) {
+        float t = 0.f;
+        if (err == cudaSuccess) err = cudaLaunchKernel(func, grid, block, a, smem, stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e0, stream);
+        for (int r = 0; r < reps && err == cudaSuccess; r++) err = cudaLaunchKernel(func, grid, block, a, smem, stream);
+        if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+        return t / reps;
+    };
+    constexpr int kNc = kCnThreads / 32, kNv = 6;
+    float tc[kNc], tv[kNv];
+    int bc = 0, bv = 0;
+    for (int i = 0; i < kNc; i++) {
+        const CnLaunch cl = cn_launch(T, n_frames, w.fmt, 32 * (i + 1));
+        tc[i] = time(cl.func, cl.grid, cl.block, args, cl.smem);
+        if (tc[i] < tc[bc]) bc = i;
+    }
+    for (int i = 0; i < kNv; i++) {
+        const VnLaunch vl = vn_launch(T, n_frames, w.fmt, i % 3 + 1, i < 3 ? 1 : kVnParts);
+        tv[i] = time(vl.func, vl.grid, dim3(kThreads), vn_args, 0);
+        if (tv[i] < tv[bv]) bv = i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "autotune_shapes");
+    for (int i = 0; i < kNc; i++)
+        if (cn_ms) cn_ms[i] = tc[i];
+    for (int i = 0; i < kNv; i++)
+        if (vn_ms) vn_ms[i] = tv[i];
+    *best = base;
+    best->cn_threads = 32 * (bc + 1);
+    best->vn_nodes = bv % 3 + 1;
+    best->vn_split = bv < 3 ? 1 : kVnParts;
+    clear_error();
+    return QCLDPC_OK;
+}
+
 extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void *workspace_dev,
                                   size_t workspace_bytes, int reps, float *cn_ms, float *vn_ms,
                                   qcldpc_stream_t stream_) {
@@ -1010,7 +1101,7 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
         if ((err = cudaEventCreate(&ev[i])) != cudaSuccess) return cuda_fail(err, "time_passes: cudaEventCreate");
     const Table &T = code->tab;
     replay_prep_kernel<<<1, 256, 0, stream>>>(w);
-    const CnLaunch cl = cn_launch(T, n_frames, w.fmt);
+    const CnLaunch cl = cn_launch(T, n_frames, w.fmt, w.cn_nt);
     Table tcopy = T;
     void *args[] = {&tcopy, &w};
     cudaEventRecord(ev[0], stream);
@@ -1019,7 +1110,7 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     cudaEventRecord(ev[1], stream);
     qc::ColsInline ccopy = code->cols_in;
     void *vn_args[] = {&tcopy, &w, &ccopy};
-    const VnLaunch vl = vn_launch(T, n_frames, w.fmt);
+    const VnLaunch vl = vn_launch(T, n_frames, w.fmt, w.vn_vpt, w.vn_split);
     for (int r = 0; r < reps && err == cudaSuccess; r++)
         err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
     cudaEventRecord(ev[2], stream);
@@ -1229,8 +1320,8 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
     void *vn_args[] = {&tcopy, &wcopy, &ccopy};
     cudaGraphConditionalHandle none = 0;
     void *ctrl_args[] = {&wcopy, &none};
-    const CnLaunch cl = cn_launch(T, F, pool->w.fmt);
-    const VnLaunch vl = vn_launch(T, F, pool->w.fmt);
+    const CnLaunch cl = cn_launch(T, F, pool->w.fmt, pool->w.cn_nt);
+    const VnLaunch vl = vn_launch(T, F, pool->w.fmt, pool->w.vn_vpt, pool->w.vn_split);
     cudaGraphNode_t prev = nullptr;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < n_passes && err == cudaSuccess; i++) {
@@ -1286,7 +1377,7 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     if (p_in) p = *p_in;
     else qcldpc_params_init(&p);
     if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format < 0 || p.msg_format > 2 ||
-        !(p.msg_step >= 0.0f) || p.soft_output)
+        !(p.msg_step >= 0.0f) || p.soft_output || !shape_ok(p))
         return fail(QCLDPC_E_INVAL, "pool_create: unsupported option");
     if (!aligned(workspace_dev, 256)) return fail(QCLDPC_E_ALIGN, "pool_create: workspace must be 256-byte aligned");
     if (int st = upload_tables(code)) return st;
@@ -1324,6 +1415,9 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;
     w.xmin = p.phi_floor * kLog2e;
     w.xmin_h = heavy_out_floor(w.clip, w.xmin);
+    w.cn_nt = p.cn_threads;
+    w.vn_vpt = p.vn_nodes;
+    w.vn_split = p.vn_split;
     w.fmt = p.msg_format;
     if (w.fmt == 2) {
         const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;

@@ -133,6 +133,8 @@ struct Work {
     int32_t ngroups;       // layered: row groups per iteration
     int32_t pass;          // check-pass kind (kPassFlood, kPassTest, kPassGroup)
     int32_t lrow0, lrows;  // kPassGroup and the group's posterior update: its base rows
+    int32_t cn_nt;         // check-block threads, 0 = chosen from Z (launch shape only)
+    int32_t vn_vpt, vn_split;  // variable pass nodes per thread / part groups, 0 = chosen
 };
 // Kinds of check pass. kPassFlood: flooding iteration t (stop test of t-1
 // when due, then the update). kPassTest: the stop test of iteration t-1

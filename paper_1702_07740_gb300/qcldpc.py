@@ -29,6 +29,7 @@ EXPORTED = [
     "qcldpc_bob_message", "qcldpc_llr",
     "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
     "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc", "qcldpc_autotune",
+    "qcldpc_autotune_shapes",
     "qcldpc_pool_workspace", "qcldpc_pool_create", "qcldpc_pool_destroy", "qcldpc_pool_state",
     "qcldpc_pool_load", "qcldpc_pool_step", "qcldpc_pools_step", "qcldpc_pool_collect",
     "qcldpc_last_error",
@@ -52,6 +53,9 @@ class qcldpc_params(ctypes.Structure):
         ("launch_mode", ctypes.c_int32),
         ("msg_step", ctypes.c_float),
         ("layers", ctypes.c_int32),
+        ("cn_threads", ctypes.c_int32),
+        ("vn_nodes", ctypes.c_int32),
+        ("vn_split", ctypes.c_int32),
     ]
 
 
@@ -112,6 +116,11 @@ def load(build_if_missing: bool = True):
                                         vp, vp, vp, vp, sz, i32, ctypes.POINTER(qcldpc_params),
                                         ctypes.POINTER(ctypes.c_float), vp]
         lib.qcldpc_autotune.restype = i32
+        lib.qcldpc_autotune_shapes.argtypes = [vp, i32, vp, sz, i32, ctypes.POINTER(qcldpc_params),
+                                               ctypes.POINTER(qcldpc_params),
+                                               ctypes.POINTER(ctypes.c_float),
+                                               ctypes.POINTER(ctypes.c_float), vp]
+        lib.qcldpc_autotune_shapes.restype = i32
         lib.qcldpc_pool_workspace.argtypes = [vp, i32, ctypes.POINTER(qcldpc_params)]
         lib.qcldpc_pool_workspace.restype = sz
         lib.qcldpc_pool_create.argtypes = [vp, i32, i32, ctypes.POINTER(qcldpc_params), vp, sz, vp,
@@ -315,6 +324,27 @@ def qcldpc_autotune(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,
     _check(st, "qcldpc_autotune")
     return best, {name: times[i] for i, name in enumerate(AUTOTUNE_CANDIDATES)
                   if times[i] == times[i]}
+
+
+# Launch-shape candidates of qcldpc_autotune_shapes, in its timing order.
+SHAPE_CN_THREADS = tuple(32 * (i + 1) for i in range(8))
+SHAPE_VN = ((1, 1), (2, 1), (3, 1), (1, 2), (2, 2), (3, 2))  # (vn_nodes, vn_split)
+
+
+def qcldpc_autotune_shapes(code: Code, n_frames: int, workspace_dev, workspace_bytes: int,
+                           params: qcldpc_params | None = None, reps: int = 5, stream=None):
+    """Fastest launch shapes on the state of the last flooding decode:
+    (best params, {cn_threads: ms}, {(vn_nodes, vn_split): ms})."""
+    best = qcldpc_params()
+    tc = (ctypes.c_float * len(SHAPE_CN_THREADS))()
+    tv = (ctypes.c_float * len(SHAPE_VN))()
+    p = ctypes.byref(params) if params is not None else None
+    st = load().qcldpc_autotune_shapes(code.handle, int(n_frames), _dev(workspace_dev, None, "workspace"),
+                                       int(workspace_bytes), int(reps), p, ctypes.byref(best), tc, tv,
+                                       _stream(stream))
+    _check(st, "qcldpc_autotune_shapes")
+    return (best, {c: tc[i] for i, c in enumerate(SHAPE_CN_THREADS)},
+            {c: tv[i] for i, c in enumerate(SHAPE_VN)})
 
 
 def qcldpc_decode_noalloc(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: int,

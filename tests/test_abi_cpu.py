@@ -34,6 +34,7 @@ def test_params_defaults():
     assert p.phi_floor == pytest.approx(1e-6)
     assert p.et_start == 1 and p.schedule == 0 and p.msg_format == 0 and p.soft_output == 0
     assert p.layers == 0
+    assert (p.cn_threads, p.vn_nodes, p.vn_split) == (0, 0, 0)  # launch shapes: library's choice
 
 
 def test_code_info_of_the_rate002_protograph():

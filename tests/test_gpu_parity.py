@@ -407,3 +407,34 @@ def test_full_size_converged_frames_satisfy_the_syndrome():
         ok = (oracle.syndrome(fr.code, chat) == fr.syn[f]).all()
         assert ok == bool(conv[f])
         np.testing.assert_array_equal(keys[f], chat[: fr.code.k])
+
+
+def test_launch_shapes_give_identical_bits_and_autotune_picks_the_fastest():
+    """Every check-block width and variable-pass shape decodes to the same
+    bits (posteriors included); qcldpc_autotune_shapes times them on the
+    state of the last decode and returns the fastest."""
+    fr = make_frames(synth.rate002_code(2000), 0.12, 4)
+    code = q.create_code_from(fr.code_dict)
+    llr = gpu_llr(fr)
+    iters = 10
+    ref = decode_soft(code, llr, fr.syn, fr.F, iters, et_start=5)
+    shapes = [dict(cn_threads=c) for c in q.SHAPE_CN_THREADS] + \
+             [dict(vn_nodes=v, vn_split=s) for v, s in q.SHAPE_VN]
+    for sh in shapes:
+        got = decode_soft(code, llr, fr.syn, fr.F, iters, et_start=5, **sh)
+        for a, b in zip(got, ref):
+            np.testing.assert_array_equal(a, b, str(sh))
+    params = q.qcldpc_params_init(soft_output=1)
+    dec = q.Decoder(code, fr.F, params, soft=True)
+    syn = dev(packed(fr.syn).view(np.int32).reshape(-1))
+    dec.decode(llr, syn, iters)
+    best, tc, tv = q.qcldpc_autotune_shapes(code, fr.F, dec.workspace, dec.ws_bytes, params, reps=3)
+    assert set(tc) == set(q.SHAPE_CN_THREADS) and set(tv) == set(q.SHAPE_VN)
+    assert all(t > 0 for t in list(tc.values()) + list(tv.values()))
+    assert best.cn_threads == min(tc, key=tc.get)
+    assert (best.vn_nodes, best.vn_split) == min(tv, key=tv.get)
+    assert best.soft_output == 1  # the other options are the caller's
+    print("shape ms:", {k: round(v, 4) for k, v in tc.items()}, {k: round(v, 4) for k, v in tv.items()})
+    for bad in (dict(cn_threads=48), dict(cn_threads=512), dict(vn_nodes=4), dict(vn_split=3)):
+        with pytest.raises(q.QcldpcError, match="INVAL"):
+            decode_soft(code, llr, fr.syn, fr.F, iters, **bad)
