@@ -163,7 +163,7 @@ typedef struct qcldpc_params {
                             messages are computed from the state at the
                             group's start and its posteriors updated before
                             the next group (an extension of the paper's
-                            flooding decoder). Pools accept flooding only */
+                            flooding decoder). Pools accept both */
     int32_t msg_format;  /* storage of the check-to-variable messages, all
                             arithmetic FP32: 0 = FP32 (default), 1 = FP16
                             (round to nearest), 2 = int8 codes q with

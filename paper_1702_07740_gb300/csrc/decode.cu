@@ -1270,9 +1270,9 @@ struct Layout2 {
     size_t llr, syn, conv, iters, state, total;
 };
 
-Layout2 pool_layout(const qcldpc_code *code, int S, int fmt) {
+Layout2 pool_layout(const qcldpc_code *code, int S, int fmt, bool layered = false) {
     Layout2 o;
-    o.base = layout_of(code->tab, S, false, fmt);
+    o.base = layout_of(code->tab, S, false, fmt, layered);
     size_t off = o.base.total;
     auto take = [&](size_t bytes) {
         size_t at = off;
@@ -1322,18 +1322,46 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
     void *ctrl_args[] = {&wcopy, &none};
     const CnLaunch cl = cn_launch(T, F, pool->w.fmt, pool->w.cn_nt);
     const VnLaunch vl = vn_launch(T, F, pool->w.fmt, pool->w.vn_vpt, pool->w.vn_split);
+    const bool layered = pool->w.layered != 0;
+    if (layered) wcopy.pass = kPassTest;
+    // layered: one Work per row group (kPassGroup, its base rows)
+    std::vector<Work> wg(layered ? pool->w.ngroups : 0, pool->w);
+    for (int k = 0; k < (int)wg.size(); k++) {
+        wg[k].pass = kPassGroup;
+        group_rows(T, pool->w.ngroups, k, &wg[k].lrow0, &wg[k].lrows);
+        wg[k].lrows -= wg[k].lrow0;
+    }
     cudaGraphNode_t prev = nullptr;
     cudaError_t err = cudaSuccess;
     for (int i = 0; i < n_passes && err == cudaSuccess; i++) {
+        // an iteration: check pass (flooding: the update and the stop test
+        // of the previous iteration; layered: the test alone), control step,
+        // then the variable pass or, per row group, its check pass and
+        // posterior update
         cudaGraphNode_t a, b, c;
         err = add_kernel(&a, g, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
                          args, cl.smem);
         if (err == cudaSuccess)
             err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),
                              ctrl_args);
-        if (err == cudaSuccess)
-            err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
-        prev = c;
+        if (!layered) {
+            if (err == cudaSuccess)
+                err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
+            prev = c;
+            continue;
+        }
+        prev = b;
+        for (int k = 0; k < (int)wg.size() && err == cudaSuccess; k++) {
+            void *gargs[] = {&tcopy, &wg[k]};
+            dim3 grid = cl.grid;
+            grid.y = (unsigned)wg[k].lrows;
+            cudaGraphNode_t x, y;
+            err = add_kernel(&x, g, &prev, 1, cl.func, grid, cl.block, gargs, cl.smem);
+            if (err == cudaSuccess)
+                err = add_kernel(&y, g, &x, 1, lvn_kernel_for(pool->w.fmt), vn_grid(T, F), dim3(kThreads),
+                                 gargs);
+            prev = y;
+        }
     }
     *last = prev;
     return err;
@@ -1360,7 +1388,7 @@ extern "C" size_t qcldpc_pool_workspace(const qcldpc_code *code, int n_slots,
     if (!code || n_slots < 1 || n_slots > 65535) return 0;
     const int fmt = p ? p->msg_format : 0;
     if (fmt < 0 || fmt > 2) return 0;
-    return pool_layout(code, n_slots, fmt).total;
+    return pool_layout(code, n_slots, fmt, p && p->schedule == 1).total;
 }
 
 extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int max_iter,
@@ -1376,12 +1404,14 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     qcldpc_params p;
     if (p_in) p = *p_in;
     else qcldpc_params_init(&p);
-    if (!(p.phi_floor > 0.0f) || p.schedule != 0 || p.msg_format < 0 || p.msg_format > 2 ||
-        !(p.msg_step >= 0.0f) || p.soft_output || !shape_ok(p))
+    if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
+        p.msg_format > 2 || !(p.msg_step >= 0.0f) || p.soft_output || !shape_ok(p) ||
+        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)))
         return fail(QCLDPC_E_INVAL, "pool_create: unsupported option");
     if (!aligned(workspace_dev, 256)) return fail(QCLDPC_E_ALIGN, "pool_create: workspace must be 256-byte aligned");
     if (int st = upload_tables(code)) return st;
-    const Layout2 lo = pool_layout(code, n_slots, p.msg_format);
+    const bool layered = p.schedule == 1;
+    const Layout2 lo = pool_layout(code, n_slots, p.msg_format, layered);
     if (workspace_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "pool_create: workspace too small");
     int dev = -1;
     cudaError_t err = cudaGetDevice(&dev);
@@ -1418,6 +1448,11 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     w.cn_nt = p.cn_threads;
     w.vn_vpt = p.vn_nodes;
     w.vn_split = p.vn_split;
+    if (layered) {
+        w.layered = 1;
+        w.ngroups = p.layers > 0 ? p.layers : code->tab.mb;
+        w.msg_buf = (int64_t)n_slots * code->tab.n_h * code->tab.Z;
+    }
     w.fmt = p.msg_format;
     if (w.fmt == 2) {
         const float step = p.msg_step > 0.0f ? p.msg_step : (p.clip > 0.0f ? p.clip : 15.0f) / 127.0f;

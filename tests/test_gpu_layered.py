@@ -141,7 +141,7 @@ def test_layered_full_size_few_iterations():
         assert_posteriors_close(post[f], ref, f"frame {f}")
 
 
-def test_layered_rejects_bad_group_counts_and_pools():
+def test_layered_rejects_bad_group_counts():
     code = q.create_code_from(synth.rate002_code(64))
     dec = q.Decoder(code, 1)
     x = torch.zeros(code.n, device="cuda")
@@ -152,8 +152,9 @@ def test_layered_rejects_bad_group_counts_and_pools():
         buf = torch.empty(ws, dtype=torch.uint8, device="cuda")
         with pytest.raises(q.QcldpcError, match="INVAL"):
             q.qcldpc_decode(code, x, s, 1, 5, params, dec.keys, dec.converged, dec.iters, buf, ws)
-    with pytest.raises(q.QcldpcError):
-        q.Pool(code, 2, 10, q.qcldpc_params_init(schedule=1))
+    for bad in (-1, code.mb + 1):
+        with pytest.raises(q.QcldpcError):
+            q.Pool(code, 2, 10, q.qcldpc_params_init(schedule=1, layers=bad))
 
 
 def test_autotune_picks_the_fastest_measured_schedule():

@@ -106,3 +106,62 @@ def test_pool_rejects_bad_arguments():
     assert q.qcldpc_pool_workspace(code, 0) == 0
     with pytest.raises(q.QcldpcError):
         q.Pool(code, 2, 10, q.qcldpc_params_init(soft_output=1))
+
+
+@pytest.mark.parametrize("groups", [7, 0])
+def test_layered_pool_slots_at_different_iterations_decode_as_alone(groups):
+    """Layered schedule in a pool: frames loaded at different times share
+    the passes (each slot at its own iteration) and decode to the same key
+    bits, flag and stop iteration as the layered decoder on each frame alone;
+    slots are reused after collection."""
+    d = synth.rate002_code(64)
+    code = q.create_code_from(d)
+    max_iter = 40
+    params = q.qcldpc_params_init(schedule=1, layers=groups)
+    frames = _frames(d, 0.12, 6, 9100)
+    alone = []
+    for llr, syn in frames:
+        dec = q.Decoder(code, 1, params)
+        dec.decode(llr, syn, max_iter)
+        torch.cuda.synchronize()
+        alone.append((dec.keys.cpu(), int(dec.converged[0]), int(dec.iters[0])))
+    pool = q.Pool(code, 4, max_iter, params)
+    ids = torch.arange(4, dtype=torch.int32, device="cuda")
+    wk = (code.k + 31) // 32
+
+    def load(slot, f):
+        q.qcldpc_pool_load(pool, 1, ids[slot:slot + 1], frames[f][0], frames[f][1])
+
+    def run_until_done(slots):
+        for _ in range(max_iter + 2):
+            if all(int(pool.state[s]) == 2 for s in slots):
+                return
+            q.qcldpc_pool_step(pool, 1)
+        raise AssertionError("slots did not finish")
+
+    def collect_and_check(slot, f):
+        keys = torch.empty(wk, dtype=torch.int32, device="cuda")
+        conv = torch.empty(1, dtype=torch.int32, device="cuda")
+        its = torch.empty(1, dtype=torch.int32, device="cuda")
+        q.qcldpc_pool_collect(pool, 1, ids[slot:slot + 1], keys, conv, its)
+        torch.cuda.synchronize()
+        ak, ac, ai = alone[f]
+        assert (int(conv), int(its)) == (ac, ai), f"frame {f}"
+        assert torch.equal(keys.cpu(), ak.view(-1)), f"frame {f}"
+
+    load(0, 0)
+    load(1, 1)
+    for _ in range(3):
+        q.qcldpc_pool_step(pool, 1)
+    load(2, 2)
+    load(3, 3)
+    run_until_done([0, 1, 2, 3])
+    for slot, f in enumerate(range(4)):
+        collect_and_check(slot, f)
+    load(0, 4)
+    q.qcldpc_pool_step(pool, 2)
+    load(1, 5)
+    run_until_done([0, 1])
+    collect_and_check(0, 4)
+    collect_and_check(1, 5)
+    assert sum(a[1] for a in alone) >= 2
