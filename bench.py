@@ -198,13 +198,6 @@ def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_bytes: in
     return cn, vn
 
 
-def iteration_bytes_survey(Z):
-    """Per-frame algorithmic bytes of one flooding iteration: heavy messages
-    read+write once (119 Z * 8), degree-1 LLRs (48 Z * 4), heavy Q and
-    posterior (2 Z * 12), syndrome (49 Z / 8)."""
-    return 119 * Z * 8 + 48 * Z * 4 + 2 * Z * 12 + 49 * Z / 8
-
-
 def source_hash():
     """Hash of the decoder's kernel sources with comments and blank space
     removed: the committed DRAM counters stay valid across comment edits and

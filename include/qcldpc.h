@@ -43,7 +43,7 @@ enum {
     QCLDPC_E_UNSUPPORTED = -8  /* code exceeds a compile-time table limit */
 };
 
-/* Table limits of this build (checked by qcldpc_create_code). The tables of
+/* Table limits (checked by qcldpc_create_code). The tables of
  * all live codes share a 64 MiB static device arena inside the library (about
  * 60 bytes per circulant plus 128 bytes per base row: 0.4 MB for a
  * 1568 x 1600 base matrix); a code takes its block on the first call that
