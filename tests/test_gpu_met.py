@@ -95,3 +95,45 @@ def test_table_arena_fills_with_nomem_and_frees_on_destroy():
     torch.cuda.synchronize()
     del codes, c
     gc.collect()
+
+
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_met_code_in_a_pool_decodes_as_alone(schedule):
+    """The 1568 x 1600 multi-edge code (column lists staged in shared memory
+    by the variable pass, variable-width check blocks) in a 3-slot pool with
+    frames loaded at different times: key bits, flag and stop iteration as
+    decoded alone, flooding and layered (8 row groups)."""
+    d = synth.met_code(16)
+    code = q.create_code_from(d)
+    fr = make_frames(d, 0.2, 3)
+    llr = gpu_llr(fr)
+    n = fr.code.n
+    syn = torch.from_numpy(synth.pack_bits(fr.syn).view(np.int32)).cuda()
+    params = q.qcldpc_params_init(schedule=schedule, layers=8 if schedule else 0)
+    max_iter = 80
+    alone = []
+    for f in range(fr.F):
+        dec = q.Decoder(code, 1, params)
+        dec.decode(llr[f * n:(f + 1) * n], syn[f], max_iter)
+        torch.cuda.synchronize()
+        alone.append((dec.keys.cpu(), int(dec.converged[0]), int(dec.iters[0])))
+    pool = q.Pool(code, 3, max_iter, params)
+    ids = torch.arange(3, dtype=torch.int32, device="cuda")
+    for f in range(fr.F):
+        q.qcldpc_pool_load(pool, 1, ids[f:f + 1], llr[f * n:(f + 1) * n], syn[f])
+        q.qcldpc_pool_step(pool, 4)
+    for _ in range(max_iter + 2):
+        if all(int(s) == 2 for s in pool.state.cpu()):
+            break
+        q.qcldpc_pool_step(pool, 1)
+    wk = (code.k + 31) // 32
+    keys = torch.empty(fr.F * wk, dtype=torch.int32, device="cuda")
+    conv = torch.empty(fr.F, dtype=torch.int32, device="cuda")
+    its = torch.empty(fr.F, dtype=torch.int32, device="cuda")
+    q.qcldpc_pool_collect(pool, fr.F, ids, keys, conv, its)
+    torch.cuda.synchronize()
+    for f in range(fr.F):
+        ak, ac, ai = alone[f]
+        assert (int(conv[f]), int(its[f])) == (ac, ai), f"frame {f}"
+        assert torch.equal(keys[f * wk:(f + 1) * wk].cpu(), ak.view(-1)), f"frame {f}"
+    assert sum(a[1] for a in alone) >= 1

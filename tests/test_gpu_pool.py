@@ -32,8 +32,8 @@ def _frames(code_dict, snr, F, seed0):
     return [(llr[f * n:(f + 1) * n], syn[f]) for f in range(F)]
 
 
-def _alone(code, llr, syn, max_iter):
-    dec = q.Decoder(code, 1)
+def _alone(code, llr, syn, max_iter, params=None):
+    dec = q.Decoder(code, 1, params)
     dec.decode(llr, syn, max_iter)
     torch.cuda.synchronize()
     return dec.keys.cpu(), int(dec.converged[0]), int(dec.iters[0])
@@ -43,15 +43,18 @@ MIX = {"r002": (synth.rate002_code, 64, 0.08), "r005": (synth.rate005_code, 100,
        "r010": (synth.rate010_code, 160, 0.35)}
 
 
-def test_server_results_equal_alone_decoding_for_a_mix_of_codes():
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_server_results_equal_alone_decoding_for_a_mix_of_codes(schedule):
+    """Flooding, and layered with one row group per base row."""
     max_iter = 60
+    params = q.qcldpc_params_init(schedule=schedule)
     codes, frames = {}, []
     for i, (name, (mk, Z, snr)) in enumerate(MIX.items()):
         d = mk(Z)
         codes[name] = q.create_code_from(d)
         for j, (llr, syn) in enumerate(_frames(d, snr, 7, 7000 + 100 * i)):
             frames.append((name, j, llr, syn))
-    srv = serve.Server(codes, {"r002": 3, "r005": 2, "r010": 4}, max_iter)
+    srv = serve.Server(codes, {"r002": 3, "r005": 2, "r010": 4}, max_iter, params)
     # arrivals spread over ticks: two frames per tick, interleaved codes
     order = sorted(frames, key=lambda t: (t[1], t[0]))
     results = {}
@@ -65,12 +68,12 @@ def test_server_results_equal_alone_decoding_for_a_mix_of_codes():
     assert len(results) == len(frames)
     n_conv = 0
     for name, j, llr, syn in frames:
-        keys, conv, iters = _alone(codes[name], llr, syn, max_iter)
+        keys, conv, iters = _alone(codes[name], llr, syn, max_iter, params)
         r = results[(name, j)]
         assert (r.converged, r.iters) == (conv, iters), (name, j)
         assert torch.equal(r.keys, keys.view(-1)), (name, j)
         n_conv += conv
-    assert 0 < n_conv < len(frames)
+    assert 0 < n_conv and (schedule == 1 or n_conv < len(frames))
 
 
 def test_pool_slots_are_reused_and_states_track_frames():
