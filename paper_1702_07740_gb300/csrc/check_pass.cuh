@@ -302,8 +302,7 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
                                                      Codec<M>::dec(pM[k][(c + 1) * nt], W));
                         d = __ffma2_rn(m, f2(-1.0f), d);  // lv - m, one rounding
                     }
-                    phi[k] = psi2(make_float2(fminf(fmaxf(fabsf(d.x), W.xmin), W.clip),
-                                              fminf(fmaxf(fabsf(d.y), W.xmin), W.clip)));
+                    phi[k] = psi2_clamped(d, W.phi_lo, W.phi_hi);
                     sga[k] = fbits(d.x);
                     sgb[k] = fbits(d.y);
                     sta ^= sga[k];
@@ -377,7 +376,7 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
 #pragma unroll
                 for (int k = 0; k < NH; k++) {
                     const float d = lv[k] - (kReadMsg ? Codec<M>::dec(pM[k][c * nt], W) : 0.0f);
-                    phi[k] = psi_f(fminf(fmaxf(fabsf(d), W.xmin), W.clip));
+                    phi[k] = psi_clamped(d, W.phi_lo, W.phi_hi);
                     sg[k] = fbits(d);
                     stot ^= sg[k];
                 }

@@ -529,6 +529,13 @@ void group_rows(const Table &T, int G, int g, int *r0, int *r1) {
     *r1 = ((g + 1) * T.mb + G - 1) / G;
 }
 
+// psi(y) = log2 coth(y ln2 / 2) in double (base-2 units; psi(inf) = 0).
+float psi_host(float y2) {
+    if (!(y2 < INFINITY)) return 0.0f;
+    const double t = std::exp2(-(double)y2);
+    return (float)std::log2((1.0 + t) / (1.0 - t));
+}
+
 // Launch-shape options: 0 (chosen by the library) or a supported value.
 bool shape_ok(const qcldpc_params &p) {
     return (p.cn_threads == 0 || (p.cn_threads >= 32 && p.cn_threads <= kCnThreads && p.cn_threads % 32 == 0)) &&
@@ -843,6 +850,8 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;  // base-2 units
     w.xmin = p.phi_floor * kLog2e;
     w.xmin_h = heavy_out_floor(w.clip, w.xmin);
+    w.phi_lo = psi_host(w.clip);
+    w.phi_hi = psi_host(w.xmin);
     w.cn_nt = p.cn_threads;
     w.vn_vpt = p.vn_nodes;
     w.vn_split = p.vn_split;
@@ -1445,6 +1454,8 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     w.clip = p.clip > 0.0f ? p.clip * kLog2e : INFINITY;
     w.xmin = p.phi_floor * kLog2e;
     w.xmin_h = heavy_out_floor(w.clip, w.xmin);
+    w.phi_lo = psi_host(w.clip);
+    w.phi_hi = psi_host(w.xmin);
     w.cn_nt = p.cn_threads;
     w.vn_vpt = p.vn_nodes;
     w.vn_split = p.vn_split;

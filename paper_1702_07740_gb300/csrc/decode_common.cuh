@@ -127,6 +127,8 @@ struct Work {
     float clip, xmin;      // base-2 units
     float xmin_h;          // floor of a heavy output's exclusive sum: max(xmin, psi(clip)),
                            // so that psi of it needs no clip (psi decreases, psi(psi(y)) = y)
+    float phi_lo, phi_hi;  // psi(clip) and psi(xmin): psi(clamp(y, xmin, clip)) =
+                           // clamp(psi(y), phi_lo, phi_hi)
     float qstep, qinv;     // int8 message quantum and its inverse (base-2 units)
     int64_t msg_buf;       // layered: elements per message buffer; 0 for flooding
     int32_t layered;       // schedule: 0 flooding, 1 layered
@@ -210,6 +212,45 @@ __device__ __forceinline__ float2 psi2(float2 y) {
     a = __ffma2_rn(a, v, f2(kA0));
     const float2 ta = __fmul2_rn(t, a);
     return make_float2(fmaxf(small.x, ta.x), fmaxf(small.y, ta.y));
+}
+
+// max of three (sm_100-class three-input form)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// psi(clamp(|y|, xmin, clip)) for a message difference y, as
+// clamp(psi(|y|), lo, hi) with lo = psi(clip), hi = psi(xmin): psi decreases,
+// so the clamp moves past it, and its lower bound merges with the max of the
+// two pieces (|y| = 0 gives +inf before the clamp, never NaN).
+__device__ __forceinline__ float psi_clamped(float y, float lo, float hi) {
+    const float a = fabsf(y);
+    const float w = a * a;
+    const float g = fmaf(fmaf(fmaf(kG3, w, kG2), w, kG1), w, kG0);
+    const float small = fmaf(w, g, kC - lg2_approx(a));
+    const float t = ex2_approx(-a);
+    const float v = t * t;
+    const float p = fmaf(fmaf(fmaf(fmaf(kA4, v, kA3), v, kA2), v, kA1), v, kA0);
+    return fminf(fmax3(small, t * p, lo), hi);
+}
+__device__ __forceinline__ float2 psi2_clamped(float2 y, float lo, float hi) {
+    const float2 a = make_float2(fabsf(y.x), fabsf(y.y));
+    const float2 w = __fmul2_rn(a, a);
+    float2 g = __ffma2_rn(f2(kG3), w, f2(kG2));
+    g = __ffma2_rn(g, w, f2(kG1));
+    g = __ffma2_rn(g, w, f2(kG0));
+    const float2 lc = __ffma2_rn(make_float2(lg2_approx(a.x), lg2_approx(a.y)), f2(-1.0f), f2(kC));
+    const float2 small = __ffma2_rn(w, g, lc);
+    const float2 t = make_float2(ex2_approx(-a.x), ex2_approx(-a.y));
+    const float2 v = __fmul2_rn(t, t);
+    float2 p = __ffma2_rn(f2(kA4), v, f2(kA3));
+    p = __ffma2_rn(p, v, f2(kA2));
+    p = __ffma2_rn(p, v, f2(kA1));
+    p = __ffma2_rn(p, v, f2(kA0));
+    const float2 tp = __fmul2_rn(t, p);
+    return make_float2(fminf(fmax3(small.x, tp.x, lo), hi), fminf(fmax3(small.y, tp.y, lo), hi));
 }
 
 // Programmatic dependent launch: let the next kernel of the graph be
