@@ -397,7 +397,13 @@ def run_ours(args, world, rank, local):
     # per step: llr + init + final, and per loop pass check pass + control +
     # variable pass (flooding) or test pass + control + 2 per row group (layered)
     per_pass = 2 + 2 * (args.layers or d["mb"]) if layered else 3
-    launches = sum(3 + per_pass * loop_passes[s % B] for s in range(args.steps))
+    # the decode graph runs flooding iterations four per trip of its loop,
+    # and the stream launch mode enqueues max_iter + 1 passes; passes after
+    # every frame stopped exit at once but still launch
+    if args.launch_mode == "stream":
+        loop_passes = [args.max_iter + 1] * B
+    unroll = 4 if (not layered and args.launch_mode != "stream") else 1
+    launches = sum(3 + per_pass * -(-loop_passes[s % B] // unroll) * unroll for s in range(args.steps))
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host.
     # Two staging buffers and a copy stream: the inputs of step s+1 are copied

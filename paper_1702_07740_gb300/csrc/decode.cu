@@ -660,39 +660,51 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
     qc::ColsInline ccopy = CI;
     void *args[] = {&tcopy, &wcopy};
     void *vn_args[] = {&tcopy, &wcopy, &ccopy};
-    cudaGraphNode_t n_cn, n_ctrl, n_vn;
     const CnLaunch cl = cn_launch(T, F, w0.fmt, w0.cn_nt);
     cudaError_t err;
     if (w0.layered) wcopy.pass = kPassTest;
-    if ((err = add_kernel(&n_cn, body, nullptr, 0, cl.func, cl.grid, cl.block, args,
-                          cl.smem)) != cudaSuccess)
-        return err;
     void *ctrl_args[] = {&wcopy, &handle};
     const bool pdl = !w0.layered;
-    if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
-                          dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
-        return err;
-    if (!w0.layered) {
-        const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
-        return add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0,
-                          true);
-    }
-    cudaGraphNode_t prev = n_ctrl;
-    for (int g = 0; g < w0.ngroups; g++) {
-        Work wg = w0;
-        wg.pass = kPassGroup;
-        group_rows(T, w0.ngroups, g, &wg.lrow0, &wg.lrows);
-        wg.lrows -= wg.lrow0;
-        void *gargs[] = {&tcopy, &wg};
-        dim3 grid = cl.grid;
-        grid.y = (unsigned)wg.lrows;
-        cudaGraphNode_t a, b;
-        if ((err = add_kernel(&a, body, &prev, 1, cl.func, grid, cl.block, gargs,
-                              cl.smem)) != cudaSuccess ||
-            (err = add_kernel(&b, body, &a, 1, lvn_kernel_for(w0.fmt), vn_grid(T, F),
-                              dim3(kThreads), gargs)) != cudaSuccess)
+    // kLoopUnroll flooding iterations per trip of the WHILE body (each trip
+    // costs a body relaunch, ~4 us on GB300): passes of frames that stopped
+    // in an earlier iteration of the trip exit at once, and the last control
+    // step decides whether another trip runs. A layered iteration is 2 + 2G
+    // launches, so its body holds one.
+    const int unroll = w0.layered ? 1 : kLoopUnroll;
+    cudaGraphNode_t prev = nullptr;
+    for (int u = 0; u < unroll; u++) {
+        cudaGraphNode_t n_cn, n_ctrl, n_vn;
+        if ((err = add_kernel(&n_cn, body, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
+                              args, cl.smem)) != cudaSuccess)
             return err;
-        prev = b;
+        if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
+                              dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
+            return err;
+        if (!w0.layered) {
+            const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
+            if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0,
+                                  true)) != cudaSuccess)
+                return err;
+            prev = n_vn;
+            continue;
+        }
+        prev = n_ctrl;
+        for (int g = 0; g < w0.ngroups; g++) {
+            Work wg = w0;
+            wg.pass = kPassGroup;
+            group_rows(T, w0.ngroups, g, &wg.lrow0, &wg.lrows);
+            wg.lrows -= wg.lrow0;
+            void *gargs[] = {&tcopy, &wg};
+            dim3 grid = cl.grid;
+            grid.y = (unsigned)wg.lrows;
+            cudaGraphNode_t a, b;
+            if ((err = add_kernel(&a, body, &prev, 1, cl.func, grid, cl.block, gargs,
+                                  cl.smem)) != cudaSuccess ||
+                (err = add_kernel(&b, body, &a, 1, lvn_kernel_for(w0.fmt), vn_grid(T, F),
+                                  dim3(kThreads), gargs)) != cudaSuccess)
+                return err;
+            prev = b;
+        }
     }
     return cudaSuccess;
 }

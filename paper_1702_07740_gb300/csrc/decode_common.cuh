@@ -77,6 +77,11 @@ constexpr int kCnThreads = QCLDPC_CN_THREADS;
 #ifndef QCLDPC_PDL
 #define QCLDPC_PDL 1
 #endif
+// Flooding iterations per trip of the decode graph's WHILE body.
+#ifndef QCLDPC_LOOP_UNROLL
+#define QCLDPC_LOOP_UNROLL 4
+#endif
+constexpr int kLoopUnroll = QCLDPC_LOOP_UNROLL;
 // Evaluate a thread's checks two at a time in packed FP32x2 arithmetic.
 #ifndef QCLDPC_CN_PAIR
 #define QCLDPC_CN_PAIR 1
