@@ -526,6 +526,7 @@ __global__ void __launch_bounds__(kCnThreads, NT ? QCLDPC_CN_TMA_MINBLOCKS : QCL
     cn_tma_kernel(const __grid_constant__ Table T, const __grid_constant__ Work W) {
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_launch_dependents();  // the control step may be scheduled; it waits for this pass
+    pdl_wait();  // after a programmatic edge: the previous variable pass is complete
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;  // block-uniform
     const bool group = W.pass == kPassGroup;

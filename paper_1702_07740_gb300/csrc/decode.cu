@@ -191,6 +191,7 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     constexpr int P = kVnParts, G = kThreads / S, NP = P / S;  // parts held per thread
     static_assert(S == 1 || S == P, "a thread holds one part or all of them");
     pdl_wait();  // the control step's flags are complete and visible
+    pdl_launch_dependents();  // the next iteration's check pass may be scheduled; it waits for this pass
     const int f = blockIdx.z;
     if (W.active[f] == 0) return;
     const int Z = T.Z;
@@ -675,7 +676,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
     for (int u = 0; u < unroll; u++) {
         cudaGraphNode_t n_cn, n_ctrl, n_vn;
         if ((err = add_kernel(&n_cn, body, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
-                              args, cl.smem)) != cudaSuccess)
+                              args, cl.smem, prev != nullptr && QCLDPC_PDL_LOOP)) != cudaSuccess)
             return err;
         if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                               dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)

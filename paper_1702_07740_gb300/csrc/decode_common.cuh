@@ -77,6 +77,11 @@ constexpr int kCnThreads = QCLDPC_CN_THREADS;
 #ifndef QCLDPC_PDL
 #define QCLDPC_PDL 1
 #endif
+// Inside a trip, the next iteration's check pass hangs off the variable pass
+// by a programmatic edge (scheduled while the variable pass drains).
+#ifndef QCLDPC_PDL_LOOP
+#define QCLDPC_PDL_LOOP 1
+#endif
 // Flooding iterations per trip of the decode graph's WHILE body.
 #ifndef QCLDPC_LOOP_UNROLL
 #define QCLDPC_LOOP_UNROLL 4
