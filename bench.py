@@ -72,6 +72,8 @@ def parse_args():
                     help="instead of the throughput line: FER per message format (fer), a "
                          "mixed-rate 256-frame batch (batch) or a serving-load sweep (serve)")
     ap.add_argument("--study-frames", type=int, default=2000, help="fer: frames per SNR")
+    ap.add_argument("--fer-formats", default="fp32,fp16,int8",
+                    help="fer: message formats to decode (comma-separated, fp32 first)")
     ap.add_argument("--fer-points", default="r002:0.13,r002:0.16,r005:0.5,r010:1.0",
                     help="fer: code:SNR operating points (codes r002, r005, r010 at n = 1e6)")
     ap.add_argument("--mix-snrs", default="0.16,0.5,1.0",

@@ -110,6 +110,8 @@ def emit(line: dict):
 
 # n = 10^6 member of each rate, for the FER study
 FER_CODES = {"met": (synth.met_code, 625, "rate 0.02 multi-edge (paper's distribution)"),
+             "met6": (lambda Z: synth.met_code(Z, girth6=True), 625,
+                      "rate 0.02 multi-edge (paper's distribution), shifts without 4-cycles"),
              "r002": (synth.rate002_code, 20000, "rate 0.02"),
              "r005": (synth.rate005_code, 50000, "rate 0.05"),
              "r010": (synth.rate010_code, 100000, "rate 0.10")}
@@ -124,8 +126,9 @@ def study_fer(args):
         mk, Z, label = FER_CODES[cname]
         code = q.create_code_from(mk(Z))
         wk = (code.k + 31) // 32
-        decs = {f: q.Decoder(code, F, q.qcldpc_params_init(msg_format=FMT[f])) for f in FMT}
-        acc = {f: {"err": [], "conv": [], "iters": [], "sec": 0.0} for f in FMT}
+        fmts = {f: FMT[f] for f in args.fer_formats.split(",")}
+        decs = {f: q.Decoder(code, F, q.qcldpc_params_init(msg_format=fmts[f])) for f in fmts}
+        acc = {f: {"err": [], "conv": [], "iters": [], "sec": 0.0} for f in fmts}
         for b in range(nb):
             llr, syn, key = make_frames(code, F, snr, seed=7_000_000 + 10_000 * si + b)
             for f, dec in decs.items():
@@ -139,10 +142,10 @@ def study_fer(args):
                 acc[f]["conv"].append(dec.converged.cpu().numpy())
                 acc[f]["iters"].append(dec.iters.cpu().numpy())
             del llr, syn, key
-        ref = np.concatenate(acc["fp32"]["err"]).astype(np.int64)
+        ref = np.concatenate(acc[next(iter(fmts))]["err"]).astype(np.int64)
         out = {"study": "fer", "code": f"{label}, Z={Z}, n={code.n}", "snr": snr,
                "max_iter": args.max_iter, "frames_per_decode": F, "formats": {}}
-        for f in FMT:
+        for f in fmts:
             e = np.concatenate(acc[f]["err"]).astype(np.int64)
             conv = np.concatenate(acc[f]["conv"])
             its = np.concatenate(acc[f]["iters"])
@@ -151,7 +154,7 @@ def study_fer(args):
                         "undetected": int(((conv == 1) & (e == 1)).sum()),
                         "mean_iters": float(its.mean()),
                         "mbps": len(e) * code.n / acc[f]["sec"] / 1e6})
-            if f != "fp32":
+            if f != "fp32" and "fp32" in fmts:
                 ent["vs_fp32"] = paired(ref, e)
             out["formats"][f] = ent
         emit(out)

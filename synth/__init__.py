@@ -78,7 +78,7 @@ MET_CN_T1 = ((15, 3), (17, 7))               # (count, type-1 degree)
 MET_CN_T2 = ((960, 2), (576, 3))             # (count, type-2 degree), each with one x3
 
 
-def met_code(Z: int, seed: int = CODE_SEED) -> dict:
+def met_code(Z: int, seed: int = CODE_SEED, girth6: bool = False) -> dict:
     """Circulant list of a QC code sampled from the paper's rate-0.02
     multi-edge degree distribution.
 
@@ -89,7 +89,10 @@ def met_code(Z: int, seed: int = CODE_SEED) -> dict:
     column 64 + r, shift 0); rows 1536..1567 the type-1 checks (15 of degree
     3, then 17 of degree 7). Within each edge type the sockets are matched by
     a seeded random permutation; sockets that land in the same base entry
-    become circulants with distinct shifts. Shifts are uniform in [0, Z).
+    become circulants with distinct shifts. Shifts are uniform in [0, Z);
+    with girth6, each heavy circulant (in seeded random order) takes a
+    uniform shift among those that close no length-4 cycle of the lifted
+    graph with the circulants placed before it (shifts_avoiding_4cycles).
     The key bits (k = 32 Z) are heavy columns 0..31.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -121,12 +124,15 @@ def met_code(Z: int, seed: int = CODE_SEED) -> dict:
     entries = {}
     for r, c in pairs:
         entries[(int(r), int(c))] = entries.get((int(r), int(c)), 0) + 1
-    out = []
-    for (r, c), k in sorted(entries.items()):
-        if k > Z:
-            raise ValueError("more circulants in one base entry than shifts")
-        for s in rng.choice(Z, size=k, replace=False):
-            out.append((r, c, int(s)))
+    if any(k > Z for k in entries.values()):
+        raise ValueError("more circulants in one base entry than shifts")
+    if girth6:
+        out = shifts_avoiding_4cycles(entries, Z, rng)
+    else:
+        out = []
+        for (r, c), k in sorted(entries.items()):
+            for s in rng.choice(Z, size=k, replace=False):
+                out.append((r, c, int(s)))
     for d in range(MET_DEG1_VN):
         out.append((d, n_heavy + d, 0))
     out.sort(key=lambda e: (e[0], e[1]))
@@ -134,6 +140,50 @@ def met_code(Z: int, seed: int = CODE_SEED) -> dict:
     return {"mb": mb, "nb": nb, "Z": Z,
             "row": arr[:, 0].astype(np.int32), "col": arr[:, 1].astype(np.int32),
             "shift": arr[:, 2].astype(np.int32)}
+
+
+def shifts_avoiding_4cycles(entries: dict, Z: int, rng) -> list:
+    """Shifts for base entries {(row, col): circulant count}, placed one
+    circulant at a time in seeded random entry order. In a QC lift a closed
+    walk e - e2 - e3 - e4 over circulants (e, e2 in one base row, e2, e3 in
+    one base column, e3, e4 in one row, e4, e in one column, consecutive
+    circulants distinct) is a length-4 cycle exactly when
+    s - s2 + s3 - s4 = 0 mod Z. A new circulant takes a uniform shift among
+    those that close no such walk with the circulants already placed and
+    differ from its entry's other shifts (uniform among the distinct ones if
+    every shift is excluded). Returns [(row, col, shift)]."""
+    keys = sorted(entries)
+    by_row, by_col, entry = {}, {}, {}
+    out = []
+    for i in rng.permutation(len(keys)):
+        r, c = keys[i]
+        for _ in range(entries[(r, c)]):
+            mine = entry.get((r, c), [])
+            bad = set(mine)
+            for c2, s2 in by_row.get(r, ()):
+                for r2, s3 in by_col.get(c2, ()):
+                    if r2 == r and s3 == s2:
+                        continue  # e3 would be e2
+                    for s4 in entry.get((r2, c), ()):
+                        if c2 == c and r2 == r and s4 == s3:
+                            continue  # e4 would be e3
+                        bad.add((s2 - s3 + s4) % Z)
+            # walks through the new circulant twice, e - e2 - e - e4, with
+            # e2 != e4 in the same entry: 2 s = s2 + s4 mod Z
+            for a in range(len(mine)):
+                for b in range(len(mine)):
+                    if a != b:
+                        t = (mine[a] + mine[b]) % Z
+                        bad.update(x for x in ((t // 2), (t + Z) // 2) if (2 * x - t) % Z == 0)
+            free = np.setdiff1d(np.arange(Z), np.fromiter(bad, dtype=np.int64, count=len(bad)))
+            if free.size == 0:
+                free = np.setdiff1d(np.arange(Z), np.array(mine, dtype=np.int64))
+            s = int(rng.choice(free))
+            by_row.setdefault(r, []).append((c, s))
+            by_col.setdefault(c, []).append((r, s))
+            entry.setdefault((r, c), []).append(s)
+            out.append((r, c, s))
+    return out
 
 
 def rate002_code(Z: int, seed: int = CODE_SEED) -> dict:
