@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from paper_1702_07740_gb300 import de
+from paper_ensemble import PAPER_CN, PAPER_VN_BALANCED as PAPER_VN, PAPER_VN_PRINTED
 
 G = de.Grid(K=512, delta=0.05)
 
@@ -65,11 +66,6 @@ def test_regular_ensembles_bracket_the_literature_threshold(dv, dc, snr_star):
     vn, cn = [(1.0, (dv,))], [(dv / dc, (dc,))]
     assert de.met_de_converges(vn, cn, snr_star * 1.015, G, max_iter=5000)
     assert not de.met_de_converges(vn, cn, snr_star * 0.985, G, max_iter=5000)
-
-
-PAPER_VN = [(7 / 400, (2, 57, 0)), (9 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
-PAPER_VN_PRINTED = [(9 / 400, (2, 57, 0)), (7 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
-PAPER_CN = [(3 / 320, (3, 0, 0)), (17 / 1600, (7, 0, 0)), (3 / 5, (0, 2, 1)), (9 / 25, (0, 3, 1))]
 
 
 def test_paper_ensemble_threshold_by_density_evolution():

@@ -12,6 +12,7 @@ import pytest
 
 import synth
 from paper_1702_07740_gb300 import pexit
+from paper_ensemble import PAPER_CN, PAPER_THRESHOLD, PAPER_VN_BALANCED, PAPER_VN_PRINTED
 
 integrate = pytest.importorskip("scipy.integrate")
 optimize = pytest.importorskip("scipy.optimize")
@@ -67,14 +68,6 @@ def test_base_matrix_counts_circulants():
     assert np.all(B[np.arange(48), np.arange(2, 50)] == 1)
 
 
-# the paper's rate-0.02 multi-edge ensemble (Sec. III-B); reading c13 swaps the
-# two heavy variable-node fractions so that type-1 sockets balance (41/400)
-PAPER_VN_BALANCED = [(7 / 400, (2, 57, 0)), (9 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
-PAPER_VN_PRINTED = [(9 / 400, (2, 57, 0)), (7 / 400, (3, 57, 0)), (24 / 25, (0, 0, 1))]
-PAPER_CN = [(3 / 320, (3, 0, 0)), (17 / 1600, (7, 0, 0)), (3 / 5, (0, 2, 1)), (9 / 25, (0, 3, 1))]
-PAPER_THRESHOLD = 2.863e-2  # Sec. III-B: density-evolution threshold of the ensemble
-
-
 def test_single_type_met_equals_protograph_exit():
     assert pexit.met_threshold([(1.0, (3,))], [(0.5, (6,))]) == pytest.approx(
         pexit.threshold(np.array([[3, 3]])), rel=2e-3)
@@ -96,3 +89,18 @@ def test_paper_ensemble_sockets_rate_and_threshold():
     assert th == pytest.approx(PAPER_THRESHOLD, rel=0.03)
     assert abs(th - PAPER_THRESHOLD) < abs(th_printed - PAPER_THRESHOLD)
     assert th > _shannon_snr(0.02)
+
+
+def test_paper_ensemble_fixture_is_the_printed_distribution():
+    """The cited fixture (Sec. III-B): its rate is 0.02 under both forms; the
+    printed heavy fractions leave the type-1 sockets unbalanced and the read
+    form balances them; the printed threshold in dB is 0.04 dB off its
+    linear value (the linear value is used)."""
+    from paper_ensemble import FIXTURE, PAPER_RATE
+    for vn in (PAPER_VN_PRINTED, PAPER_VN_BALANCED):
+        assert pexit.met_rate(vn, PAPER_CN) == pytest.approx(PAPER_RATE)
+    sockets = lambda types, t: sum(w * d[t] for w, d in types)
+    assert sockets(PAPER_VN_BALANCED, 0) == pytest.approx(sockets(PAPER_CN, 0)) == pytest.approx(41 / 400)
+    assert sockets(PAPER_VN_PRINTED, 0) == pytest.approx(39 / 400)
+    assert 10 * np.log10(FIXTURE["threshold_snr"]) == pytest.approx(-15.43, abs=0.005)
+    assert FIXTURE["threshold_db_printed"] == -15.47
