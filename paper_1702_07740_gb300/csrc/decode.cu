@@ -30,11 +30,13 @@
 //               iteration t-1 are kept: vn_kernel skips them) and sets the
 //               graph's loop condition.
 //   vn_kernel   per heavy variable v: L_v = Q_v + sum over its ~60 circulants
-//               of m_cv, read at offsets (j - s) mod Z (coalesced, one wrap).
+//               of m_cv, read at offsets (j - s) mod Z (coalesced, one wrap),
+//               as two interleaved partial sums added in a fixed order.
 // A last pass (t = max_iter + 1) runs cn_tma_kernel as a pure stop test.
-// Inside the decode graph the control and variable passes hang off
-// programmatic edges: they are scheduled while their predecessor drains and
-// wait for its results on the device.
+// The decode graph's WHILE body holds four flooding iterations (passes of
+// frames that already stopped exit at once). Within it every pass hangs off
+// its predecessor by a programmatic edge: it is scheduled while the
+// predecessor drains and waits for its results on the device.
 //
 // Layered schedule (an extension; schedule = 1): the base rows form G groups
 // visited in order. An iteration is a stop-test pass (cn_tma_kernel, test
