@@ -8,7 +8,7 @@ The arithmetic lives in ``qcldpc_oracle.c`` (plain C99, IEEE double, no
 fused multiply-add); this module only compiles it with gcc and marshals numpy
 arrays. Brute-force references for tiny codes are in ``oracle.brute``.
 
-Paper: arXiv 1702.07740. Sec. III-D (QC expansion), Sec. II-C (Bob's message
+Paper: arXiv 1702.07740. Sec. III-C (QC expansion), Sec. II-C (Bob's message
 and the d-dimensional division), Algorithm 1 (sum-product decoding).
 """
 from __future__ import annotations
@@ -80,7 +80,7 @@ def _ptr(a: np.ndarray):
 
 
 class Code:
-    """Expanded QC code: the edge list of H (Sec. III-D).
+    """Expanded QC code: the edge list of H (Sec. III-C).
 
     ``row, col, shift`` list the circulants of the base matrix; circulant h
     yields edges e = h*Z + i between check row*Z + i and variable

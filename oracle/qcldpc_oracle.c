@@ -13,7 +13,7 @@
  *
  * Sources (arXiv 1702.07740, "Key reconciliation with LDPC codes for
  * long-distance quantum cryptography"):
- *   - QC expansion: Sec. III-D (quasi-cyclic codes). A base entry of value
+ *   - QC expansion: Sec. III-C (quasi-cyclic codes). A base entry of value
  *     i becomes the identity shifted right by i-1; with shift s = i-1 row j
  *     of the block has its one at column (j+s) mod Z.
  *   - Bob's message M_i = (-1)^{C_i} Y_i and its d-dimensional form
@@ -50,7 +50,7 @@
 #include <string.h>
 
 /* ------------------------------------------------------------------------ */
-/* QC expansion (Sec. III-D)                                                 */
+/* QC expansion (Sec. III-C)                                                 */
 /* ------------------------------------------------------------------------ */
 
 /* Circulant h = (row r, column c, shift s) contributes, for every i in [0,Z),

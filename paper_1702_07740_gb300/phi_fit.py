@@ -18,7 +18,8 @@ psi is split at y = 1/ln2 (x = 1):
 The coefficients are near-minimax fits in relative error (Lawson reweighting
 of least squares on Chebyshev nodes) against mpmath references of the two
 series. Run ``python -m paper_1702_07740_gb300.phi_fit`` to print them; the
-values in ``csrc/decode.cu`` come from this script. A development-time helper:
+values in ``csrc/decode_common.cuh`` come from this script
+(tests/test_phi_fit_cpu.py checks that they match). A development-time helper:
 the library never imports it.
 """
 from __future__ import annotations

@@ -12,7 +12,7 @@ Workload recipe (stand-in for the paper's codes, which are not published):
   replacement, a second circulant with a different shift (``per_row`` > 1
   gives every row that many circulants instead). The remaining columns are
   degree-1 identity blocks on rows 0, 1, ... (shift 0), forming the long
-  unshifted diagonal of Sec. III-D. Shifts are uniform in [0, Z).
+  unshifted diagonal of Sec. III-C. Shifts are uniform in [0, Z).
 * ``met_code``: a QC code sampled from the paper's rate-0.02 multi-edge
   degree distribution (Sec. III-B), 1600 base columns, 1568 base rows.
 * ``channel_frame``: x ~ N(0,1), z ~ N(0, 1/snr), y = x + z (the virtual
