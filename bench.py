@@ -66,6 +66,9 @@ def parse_args():
     ap.add_argument("--msg-format", choices=["fp32", "fp16", "int8"], default="fp32",
                     help="storage of edge messages (arithmetic stays FP32)")
     ap.add_argument("--schedule", choices=["flooding", "layered"], default="flooding")
+    ap.add_argument("--vn-pass", choices=["accumulate", "separate"], default="accumulate",
+                    help="flooding posteriors: integer sums accumulated by the check pass, or a "
+                         "separate variable pass re-reading every message")
     ap.add_argument("--layers", type=int, default=0,
                     help="layered: row groups per iteration (0 = one per base row)")
     ap.add_argument("--study", choices=["fer", "batch", "serve", "schedule", "et"], default=None,
@@ -185,19 +188,35 @@ class ClockSampler:
 
 # ------------------------------------------------------- algorithmic bytes
 
-def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_bytes: int = 4):
-    """Bytes one frame's check-node / variable-node pass must move (FP32).
+def pass_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_bytes: int = 4,
+               accumulate: bool = True):
+    """Bytes one frame's check-node / variable-node pass must move.
 
-    Check pass: read and write every heavy message (n_h Z floats each way),
+    Check pass: read and write every heavy message (n_h Z messages each way),
     read the degree-1 Phi values (n_d1 Z floats), the heavy posteriors once
     (n_hcols Z floats), the syndrome (mb Z bits) and previous degree-1
     decisions (n_d1 Z bits), write new decisions (n_d1 Z bits).
-    Variable pass: read every heavy message once, the heavy channel LLRs, and
-    write the heavy posteriors.
+    Variable pass, separate: read every heavy message once, the heavy channel
+    LLRs, and write the heavy posteriors (stored twice, 2 x 4 bytes).
+    Variable pass, accumulated: read the two integer partial sums of every
+    heavy node and clear them (16 bytes), read its channel LLR and write its
+    posterior twice.
     """
     cn = 2 * msg_bytes * n_h * Z + 4 * (n_d1 * Z + n_hcols * Z) + (mb * Z + 2 * n_d1 * Z) / 8
-    vn = msg_bytes * n_h * Z + 4 * 2 * n_hcols * Z
+    if accumulate:
+        vn = (16 + 4 + 8) * n_hcols * Z
+    else:
+        vn = msg_bytes * n_h * Z + 4 * 2 * n_hcols * Z
     return cn, vn
+
+
+def iteration_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_bytes: int = 4):
+    """Algorithmic bytes of one flooding iteration of one frame: every heavy
+    message read and written once, the degree-1 Phi values read, the heavy
+    posteriors read and written with their channel LLRs, the syndrome and the
+    degree-1 decisions in and out."""
+    return (2 * msg_bytes * n_h * Z + 4 * n_d1 * Z + 12 * n_hcols * Z
+            + (mb * Z + 2 * n_d1 * Z) / 8)
 
 
 def source_hash():
@@ -255,6 +274,37 @@ def oracle_sample(Z, snr, iters, seed, d=None):
     return code.n, t1 - t0, (t2 - t1) / max(iters, 1)
 
 
+def oracle_sample_threads(Z, snr, iters, seed, threads, d=None):
+    """Time the FP64 oracle on `threads` frames at once, one per host thread
+    (the C oracle runs with the interpreter lock released, so the threads
+    run on separate cores): each thread maps and decodes its own copy of
+    one frame for `iters` iterations. Returns (bits decoded, wall time of
+    the maps, wall time per iteration)."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    d = synth.rate002_code(Z) if d is None else d
+    code = oracle.Code.from_dict(d)
+    x, y, bits = synth.channel_frame(code.n, snr, seed)
+    m32 = oracle.bob_message(y, bits).astype(np.float32)
+    syn = oracle.syndrome(code, bits)
+    x64, m64 = x.astype(np.float32).astype(np.float64), m32.astype(np.float64)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        t0 = time.perf_counter()
+        qs = list(ex.map(lambda _: oracle.llr(x64, m64, snr), range(threads)))
+        t1 = time.perf_counter()
+        list(ex.map(lambda qf: oracle.decode(code, qf, syn, iters, et_start=iters + 1), qs))
+        t2 = time.perf_counter()
+    return threads * code.n, t1 - t0, (t2 - t1) / max(iters, 1)
+
+
+def host_cores():
+    """Cores this process may run on (the box's nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def oracle_rate(n, t_map, t_iter, iters_per_frame):
     """Raw Mbit/s of the oracle, extrapolated to iters_per_frame iterations."""
     return n / (t_map + t_iter * iters_per_frame) / 1e6
@@ -266,10 +316,12 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     sample_iters = 2
+    cores = host_cores()
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        n, t_map, t_iter = oracle_sample(args.Z, args.snr, sample_iters, synth.frame_seed(s))
+        n, t_map, t_iter = oracle_sample_threads(args.Z, args.snr, sample_iters, synth.frame_seed(s),
+                                                 cores)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append((n, t_map, t_iter, dt))
@@ -277,17 +329,18 @@ def run_reference(args, world, rank):
     t_iter = float(np.mean([t[2] for t in times]))
     n = times[0][0]
     value = oracle_rate(n, t_map, t_iter, args.max_iter)
-    sample = (f"per step: 1 frame (n={n}), 8-D map + {sample_iters} flooding iterations of the "
-              f"FP64 oracle, extrapolated to {args.max_iter} iterations per frame")
+    sample = (f"per step: {cores} frames (n={n // cores}) on {cores} host threads, 8-D map + "
+              f"{sample_iters} flooding iterations of the FP64 oracle each, extrapolated to "
+              f"{args.max_iter} iterations per frame")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * float(np.mean([t[3] for t in times])),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
-        "config": {"workload": WORKLOAD, "Z": args.Z, "n": n, "snr": args.snr,
+        "config": {"workload": WORKLOAD, "Z": args.Z, "n": n // cores, "snr": args.snr,
                    "max_iter": args.max_iter},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -313,7 +366,8 @@ def run_ours(args, world, rank, local):
     params = q.qcldpc_params_init(launch_mode=1 if args.launch_mode == "stream" else 0,
                                   msg_format={"fp32": 0, "fp16": 1, "int8": 2}[args.msg_format],
                                   schedule=1 if args.schedule == "layered" else 0,
-                                  layers=args.layers)
+                                  layers=args.layers,
+                                  vn_pass=0 if args.vn_pass == "accumulate" else 1)
     layered = args.schedule == "layered"
 
     # --- seeded inputs, resident in HBM before timing
@@ -473,9 +527,11 @@ def run_ours(args, world, rank, local):
     cn_ms, vn_ms = q.qcldpc_time_passes(code, F, ws, ws_bytes, args.reps, stream)
     col_count = np.bincount(d["col"], minlength=d["nb"])
     heavy = col_count != 1
-    cn_b, vn_b = pass_bytes(d["Z"], n_h=int(heavy[d["col"]].sum()),
-                            n_d1=int((~heavy[d["col"]]).sum()), n_hcols=int(heavy.sum()),
-                            mb=d["mb"], msg_bytes={"fp32": 4, "fp16": 2, "int8": 1}[args.msg_format])
+    shape = dict(Z=d["Z"], n_h=int(heavy[d["col"]].sum()), n_d1=int((~heavy[d["col"]]).sum()),
+                 n_hcols=int(heavy.sum()), mb=d["mb"],
+                 msg_bytes={"fp32": 4, "fp16": 2, "int8": 1}[args.msg_format])
+    cn_b, vn_b = pass_bytes(**shape, accumulate=args.vn_pass == "accumulate" and not layered)
+    it_b = iteration_bytes(**shape)
     peaks, peak_kind = measured_peaks()
     dom, dom_ms, dom_bytes = (("check_pass", cn_ms, cn_b * F) if cn_ms >= vn_ms
                               else ("variable_pass", vn_ms, vn_b * F))
@@ -493,11 +549,17 @@ def run_ours(args, world, rank, local):
     mean_iters = float(np.mean(iters_all))
     if world == 1 and not args.no_cpu_baseline:
         nn, t_map, t_iter = oracle_sample(args.Z, args.snr, args.cpu_iters, synth.frame_seed(0), d)
-        cpu = {"value": oracle_rate(nn, t_map, t_iter, mean_iters), "unit": UNIT, "cores": 1,
+        one = oracle_rate(nn, t_map, t_iter, mean_iters)
+        cores = host_cores()
+        na, ta_map, ta_iter = oracle_sample_threads(args.Z, args.snr, args.cpu_iters,
+                                                    synth.frame_seed(0), cores, d)
+        cpu = {"value": oracle_rate(na, ta_map, ta_iter, mean_iters), "unit": UNIT, "cores": cores,
                "kind": "oracle",
-               "sample": (f"1 frame (n={nn}): FP64 8-D map + {args.cpu_iters} flooding "
-                          f"iterations, extrapolated to the GPU run's mean {mean_iters:.1f} "
-                          f"iterations per frame; single-threaded C")}
+               "sample": (f"{cores} frames (n={nn}) on {cores} host threads, one frame each: FP64 "
+                          f"8-D map + {args.cpu_iters} flooding iterations, extrapolated to the GPU "
+                          f"run's mean {mean_iters:.1f} iterations per frame"),
+               "single_core": {"value": one, "cores": 1,
+                               "sample": f"1 frame, same map and iterations, one thread"}}
 
     lo, hi = wilson(frame_err, frames_total)
     line = {
@@ -505,7 +567,7 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "msg_format": args.msg_format,
+        "msg_format": args.msg_format, "vn_pass": args.vn_pass if not layered else None,
         "schedule": args.schedule if not layered else f"layered, {args.layers or d['mb']} row groups",
         "config": {"workload": WORKLOAD if args.code == "rate002" else
                    "met_rate0.02_n1e6_snr%g_max%dit_%dframes" % (args.snr, args.max_iter, F),
@@ -529,7 +591,12 @@ def run_ours(args, world, rank, local):
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs",
                      "cn_ms": cn_ms, "vn_ms": vn_ms,
-                     "bytes_per_launch": dom_bytes},
+                     "bytes_per_launch": dom_bytes,
+                     # whole flooding iterations of the timed run: algorithmic
+                     # bytes of a frame-iteration x frame-iterations per step
+                     # / device time per step, of the same peak
+                     "iteration_frac": (it_b * F * mean_iters / (elapsed / args.steps) / 1e9 / peak
+                                        if not layered else None)},
         "clocks": clocks,
     }
     if cpu:

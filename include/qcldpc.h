@@ -58,8 +58,9 @@ enum {
 typedef struct qcldpc_code qcldpc_code; /* opaque, library-owned */
 
 /*
- * Build a QC code from its base-matrix circulant list (Sec. III-D: every base
- * entry of value i is replaced by the Z x Z identity shifted right by i-1).
+ * Build a QC code from its base-matrix circulant list (QC expansion, Sec.
+ * III-C). Each circulant is a Z x Z permutation block given by its shift
+ * s in [0, Z): row i of the block has its single one in column (i + s) mod Z.
  * Circulant h = (circ_row[h], circ_col[h], circ_shift[h]) puts, for every
  * i in [0, Z), a one at (check circ_row*Z + i, variable circ_col*Z +
  * (i + circ_shift) mod Z). Several circulants may share a base entry if their
@@ -72,9 +73,11 @@ typedef struct qcldpc_code qcldpc_code; /* opaque, library-owned */
  *   out         receives the new handle (set to NULL on failure)
  *
  * Columns holding exactly one circulant are degree-1 ("diagonal") columns:
- * their variable nodes never need per-iteration messages (Sec. III-D). All
- * other columns are heavy columns. Host-only: the tables travel to the GPU
- * as kernel parameters, so no device memory is allocated. The handle
+ * their variable nodes never need per-iteration messages (the unshifted
+ * diagonal of Sec. III-C). All other columns are heavy columns. Host-only:
+ * no device memory is allocated here; the tables are copied into the
+ * library's static device table arena on the first call that launches work
+ * with the code, and their block is returned by qcldpc_destroy_code. The handle
  * remembers the CUDA device current at creation (decoding on another device
  * fails with QCLDPC_E_INVAL). Errors: QCLDPC_E_INVAL, _SHIFT_RANGE,
  * _DUP_SHIFT, _UNSUPPORTED, _NOMEM.
@@ -190,6 +193,17 @@ typedef struct qcldpc_params {
     int32_t vn_split;    /* variable pass: 1 = a thread adds both partial sums
                             of its nodes, 2 = two thread groups, one per
                             partial sum (added in the same order) */
+    int32_t vn_pass;     /* how flooding forms the posteriors L_v = Q_v +
+                            sum_c m_cv (Algorithm 1, Step 3). 0 (default):
+                            the check pass adds every new heavy message,
+                            rounded to a fixed-point grid (2^-20 for the
+                            rate-0.02 codes; the int8 quantum for int8
+                            storage), into exact integer per-node sums, so
+                            one iteration reads and writes each message once;
+                            the sums do not depend on the order of the adds.
+                            1: a separate variable pass re-reads every message
+                            and adds them in FP32 (vn_nodes and vn_split
+                            apply). Layered decoding ignores it */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);

@@ -1,6 +1,6 @@
 // Code construction, status reporting and option defaults of the qcldpc C ABI.
 //
-// QC expansion (arXiv 1702.07740, Sec. III-D): a base entry holding shift s
+// QC expansion (arXiv 1702.07740, Sec. III-C): a base entry holding shift s
 // stands for the Z x Z identity shifted right by s, so row i of the block has
 // its one at column (i + s) mod Z. The expansion is never materialised: the
 // kernels address messages as (circulant, offset) and compute (i + s) mod Z
@@ -165,6 +165,7 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->cn_threads = 0;
     p->vn_nodes = 0;
     p->vn_split = 0;
+    p->vn_pass = 0;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,

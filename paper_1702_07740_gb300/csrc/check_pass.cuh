@@ -34,6 +34,7 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
     const M *msg_rd = static_cast<const M *>(W.msg) + ((t - 1) & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
     M *msg = static_cast<M *>(W.msg) + (t & 1) * W.msg_buf + (size_t)f * T.n_h * Z;
     const float *L = W.L + (size_t)f * T.n_hcols * 2 * Z;
+    int32_t *acc = W.acc + (size_t)f * T.n_hcols * 2 * Z;
     const float *phiq = W.phiq + (size_t)f * T.n_d1 * Z;
     const size_t bstride = (size_t)T.n_d1 * ZW;
     uint32_t *bcur = W.bits + ((size_t)(t & 1) * W.n_frames + f) * bstride;
@@ -87,7 +88,11 @@ __device__ __forceinline__ bool cn_row_generic(const Table &T, const Work &W, in
             const uint32_t sk = (stot ^ sg[k]) & kSign;
             if (k < nh) {
                 const float mag = fminf(psi_f(ex), W.clip);
-                if (valid) msg[ob + i] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
+                const M e = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
+                if (valid) {
+                    msg[ob + i] = e;
+                    if (W.accum) red_add(acc + oa + i, acc_value(e, W));
+                }
             } else {
                 const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
                 const uint32_t word = __ballot_sync(0xffffffffu, valid && dbits != 0);
@@ -134,8 +139,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                  : "memory");
 }
 
+// One bounded test of the barrier's phase. With QCLDPC_WAIT_HINT_NS > 0 the
+// waiting thread may be suspended for up to that many nanoseconds (it wakes
+// when the phase completes), so a warp re-polls far less often while the
+// copies are in flight.
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
+#if QCLDPC_WAIT_HINT_NS > 0
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "n"(QCLDPC_WAIT_HINT_NS)
+        : "memory");
+#else
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -143,6 +161,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "=r"(ok)
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
+#endif
     return ok != 0;
 }
 
@@ -204,8 +223,8 @@ __device__ __noinline__ void soft_deg1(const Table &T, const Work &W, int f, int
 // the staged rows arrived. Thread tid < nt owns checks i0 + c nt + tid.
 template <int NH, int ND, int MODE, typename M, int NT, bool SYN_SMEM, typename Wait>
 __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f, int r, int rp, int t,
-                                           int i0, const int *ob, const int *s_off, const float *stage,
-                                           const uint32_t *sy0, int b0, Wait wait) {
+                                           int i0, const int *oa, const int *ob, const int *s_off,
+                                           const float *stage, const uint32_t *sy0, int b0, Wait wait) {
     constexpr int D = NH + ND;
     constexpr int NHa = NH > 0 ? NH : 1;
     constexpr int NDa = ND > 0 ? ND : 1;
@@ -242,7 +261,9 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
                 pB[k] = reinterpret_cast<const uint32_t *>(stage) + s_off[q++] + (tid >> 5);
         }
     }
-    // Output rows at this thread's first check.
+    // Output rows at this thread's first check; oA: the heavy nodes'
+    // accumulators at the posterior offsets (node (i + s) mod Z collects at
+    // i + s, below 2Z).
     M *oM[NHa];
     uint32_t *oB[NDa];
     {
@@ -253,6 +274,9 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
             else oB[k - NH] = bcur + ob[k] + (i0 >> 5) + (tid >> 5);
         }
     }
+    // accumulator of heavy entry k for this thread's check c: accb + oa[k] + c nt
+    int32_t *accb = W.acc + (size_t)f * T.n_hcols * 2 * Z + i0 + tid;
+    const bool accum = W.accum != 0;
     // syndrome words of the owned checks (check c of this thread sits c * ws
     // words after the first), loaded while the copies are in flight
     const int sb = b0 + tid;
@@ -334,8 +358,14 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
                     if (k < NH) {
                         // min(psi(max(s, xmin)), clip) = psi(max(s, xmin_h))
                         const float2 mag = psi2(make_float2(fmaxf(s2.x, W.xmin_h), fmaxf(s2.y, W.xmin_h)));
-                        if (va) oM[k][c * nt] = Codec<M>::enc(__uint_as_float(fbits(mag.x) ^ ska), W);
-                        if (vb) oM[k][(c + 1) * nt] = Codec<M>::enc(__uint_as_float(fbits(mag.y) ^ skb), W);
+                        const M ea = Codec<M>::enc(__uint_as_float(fbits(mag.x) ^ ska), W);
+                        const M eb = Codec<M>::enc(__uint_as_float(fbits(mag.y) ^ skb), W);
+                        if (va) oM[k][c * nt] = ea;
+                        if (vb) oM[k][(c + 1) * nt] = eb;
+                        if (accum) {
+                            if (va) red_add(accb + (oa[k] + c * nt), acc_value(ea, W));
+                            if (vb) red_add(accb + (oa[k] + (c + 1) * nt), acc_value(eb, W));
+                        }
                     } else {
                         const float2 ex = make_float2(fmaxf(s2.x, W.xmin), fmaxf(s2.y, W.xmin));
                         const uint32_t da = ex.x < phi[k].x ? ska : (sga[k] & kSign);
@@ -400,7 +430,11 @@ __device__ __forceinline__ bool cn_compute(const Table &T, const Work &W, int f,
                     const uint32_t sk = (stot ^ sg[k]) & kSign;  // sign of m_cv
                     if (k < NH) {
                         const float mag = psi_f(fmaxf(s1, W.xmin_h));
-                        if (valid) oM[k][c * nt] = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
+                        const M e = Codec<M>::enc(__uint_as_float(fbits(mag) ^ sk), W);
+                        if (valid) {
+                            oM[k][c * nt] = e;
+                            if (accum) red_add(accb + (oa[k] + c * nt), acc_value(e, W));
+                        }
                     } else {
                         const float ex = fmaxf(s1, W.xmin);
                         const uint32_t dbits = ex < phi[k] ? sk : (sg[k] & kSign);
@@ -493,7 +527,7 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
 
     const int cb0 = r * Z + i0;
     const bool bad = cn_compute<NH, ND, MODE, M, NT, false>(
-        T, W, f, r, rp, t, i0, ob, s_off, stage, W.syn + (size_t)f * W.words_m + (cb0 >> 5), cb0 & 31,
+        T, W, f, r, rp, t, i0, oa, ob, s_off, stage, W.syn + (size_t)f * W.words_m + (cb0 >> 5), cb0 & 31,
         [&] { return stage_wait(bar, W); });
     __syncthreads();
     if (tid == 0) mbar_inval(bar);

@@ -9,7 +9,7 @@
 //                       twice in a row so reads at (i + s) need no wrap
 //   phiq [n_d1][Z]      +-Phi(|Q_p|) of every degree-1 variable node, indexed
 //                       by (degree-1 circulant, check offset); its message to
-//                       the check never changes (Sec. III-D, long diagonal)
+//                       the check never changes (Sec. III-C, long diagonal)
 //   bits [2][n_d1][ZW]  hard decisions of the degree-1 nodes, double
 //                       buffered by iteration parity (ZW = ceil(Z/32) words)
 // Every array carries kSlack elements of padding at its end, so that lanes
@@ -92,6 +92,11 @@ __global__ void __launch_bounds__(kThreads) init_kernel(const __grid_constant__ 
         float *row = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
         row[j] = qv;
         row[j + Z] = qv;
+        if (W.accum) {
+            int32_t *a = W.acc + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+            a[j] = 0;
+            a[j + Z] = 0;
+        }
     }
     // degree-1 nodes: one warp per (frame, circulant, 32-check word)
     const int lane = threadIdx.x & 31;
@@ -305,6 +310,46 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
     }
 }
 
+// Variable pass of flooding with accumulated posteriors (accum = 1): for
+// every heavy node v = (column hc, j), L_v = Q_v + acc_inv (acc[j] +
+// acc[j + Z]), the exact integer sum of the fixed-point messages the check
+// pass just added, written twice (j and j + Z); both accumulator words are
+// cleared for the next iteration. Frames that stopped keep the posteriors of
+// their last test. Grid (tile of kPostVpt * kThreads nodes, heavy column,
+// frame).
+// The words are read and cleared with atomic exchanges, which the L2 serves
+// where the reductions landed: on GB300 plain loads of words that many SMs
+// have just reduced into took more than twice as long (18 us against 7.5 us
+// for 16 frames of the n = 10^6 code, measured in isolation).
+constexpr int kPostVpt = 2;
+__global__ void __launch_bounds__(kThreads) post_kernel(const __grid_constant__ Table T,
+                                                        const __grid_constant__ Work W) {
+    pdl_wait();  // the control step's flags (and the check pass's sums) are complete and visible
+    pdl_launch_dependents();  // the next iteration's check pass may be scheduled; it waits for this pass
+    const int f = blockIdx.z;
+    if (W.active[f] == 0) return;
+    const int Z = T.Z;
+    const int hc = blockIdx.y;
+    const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
+    float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+    int32_t *__restrict__ a = W.acc + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+#pragma unroll
+    for (int u = 0; u < kPostVpt; u++) {
+        const int j = (blockIdx.x * kPostVpt + u) * kThreads + threadIdx.x;
+        if (j < Z) {
+            const int sum = atomicExch(a + j, 0) + atomicExch(a + j + Z, 0);
+            const float lvj = fmaf((float)sum, W.acc_inv, __ldg(q + j) * kLog2e) + 0.0f;  // -0 -> +0
+            L[j] = lvj;
+            L[j + Z] = lvj;
+        }
+    }
+}
+
+dim3 post_grid(const Table &T, int F) {
+    const int span = kThreads * kPostVpt;
+    return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)(T.n_hcols > 0 ? T.n_hcols : 1), (unsigned)F);
+}
+
 // Layered schedule, posterior update of one row group: for every heavy
 // variable v, L_v += sum over the group's circulants of v's column of
 // (m_cv(t) - m_cv(t-1)), read at (j - s) mod Z from the two message buffers
@@ -419,7 +464,7 @@ __global__ void replay_prep_kernel(const __grid_constant__ Work W) {
 // ------------------------------------------------------------ host side
 
 struct Layout {
-    size_t t, err, active, fail, msg, L, phiq, bits, post1, total;
+    size_t t, err, active, fail, msg, L, acc, phiq, bits, post1, total;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -434,16 +479,19 @@ Layout layout_of(const Table &T, int F, bool soft, int fmt, bool layered = false
         off = align_up(off + bytes, 256);
         return at;
     };
-    const size_t Z = (size_t)T.Z, ZW = (Z + 31) / 32;
-    o.t = take(sizeof(int32_t) * F);
+    // element counts in size_t (F up to 65535 times a frame's arrays)
+    const size_t Z = (size_t)T.Z, ZW = (Z + 31) / 32, Fs = (size_t)F;
+    const size_t nh = (size_t)T.n_h, nhc = (size_t)T.n_hcols, nd1 = (size_t)T.n_d1;
+    o.t = take(sizeof(int32_t) * Fs);
     o.err = take(sizeof(int32_t));
-    o.active = take(sizeof(int32_t) * F);
-    o.fail = take(sizeof(int32_t) * F);
-    o.msg = take(msg_elem_size(fmt) * ((layered ? 2 : 1) * F * T.n_h * Z + kSlack));
-    o.L = take(sizeof(float) * (F * T.n_hcols * 2 * Z + kSlack));
-    o.phiq = take(sizeof(float) * (F * T.n_d1 * Z + kSlack));
-    o.bits = take(sizeof(uint32_t) * (2 * F * T.n_d1 * ZW + kSlack));
-    o.post1 = soft ? take(sizeof(float) * (2 * F * T.n_d1 * Z + kSlack)) : 0;
+    o.active = take(sizeof(int32_t) * Fs);
+    o.fail = take(sizeof(int32_t) * Fs);
+    o.msg = take(msg_elem_size(fmt) * ((layered ? 2 : 1) * Fs * nh * Z + kSlack));
+    o.L = take(sizeof(float) * (Fs * nhc * 2 * Z + kSlack));
+    o.acc = layered ? 0 : take(sizeof(int32_t) * (Fs * nhc * 2 * Z + kSlack));
+    o.phiq = take(sizeof(float) * (Fs * nd1 * Z + kSlack));
+    o.bits = take(sizeof(uint32_t) * (2 * Fs * nd1 * ZW + kSlack));
+    o.post1 = soft ? take(sizeof(float) * (2 * Fs * nd1 * Z + kSlack)) : 0;
     o.total = off;
     return o;
 }
@@ -543,7 +591,37 @@ float psi_host(float y2) {
 bool shape_ok(const qcldpc_params &p) {
     return (p.cn_threads == 0 || (p.cn_threads >= 32 && p.cn_threads <= kCnThreads && p.cn_threads % 32 == 0)) &&
            (p.vn_nodes >= 0 && p.vn_nodes <= kVnVptMax) &&
-           (p.vn_split == 0 || p.vn_split == 1 || p.vn_split == kVnParts);
+           (p.vn_split == 0 || p.vn_split == 1 || p.vn_split == kVnParts) &&
+           (p.vn_pass == 0 || p.vn_pass == 1);
+}
+
+// Fixed-point grid of the posterior accumulators (base-2 units): the
+// finest 2^-k, k <= 24, for which the full sum of a heavy column's
+// messages fits in int32 when every message has the largest magnitude the
+// check pass can store, psi(xmin_h) (the clip folded into the floor), with
+// 1% slack for FP32 evaluation and FP16 rounding. 0 when no k >= 8 fits.
+float acc_scale_for(const qcldpc_code *code, float clip2, float xmin_h2) {
+    int maxcol = 1;
+    const std::vector<int32_t> &cp = code->host.col_ptr;
+    for (size_t h = 0; h + 1 < cp.size(); h++) maxcol = std::max(maxcol, cp[h + 1] - cp[h]);
+    const double t = std::exp2(-(double)xmin_h2);
+    const double mmax = std::min((double)clip2, std::log2((1.0 + t) / (1.0 - t))) * 1.01;
+    const int k = std::min(24, (int)std::floor(std::log2(2147483647.0 / ((double)maxcol * mmax))));
+    return k >= 8 ? std::ldexp(1.0f, k) : 0.0f;
+}
+
+// Work fields of the accumulated-posterior flooding pass (vn_pass = 0).
+void set_accum(const qcldpc_code *code, const qcldpc_params &p, char *acc_base, Work &w) {
+    if (w.layered || p.vn_pass != 0) return;
+    if (w.fmt == 2) {
+        w.acc_inv = w.qstep;  // the sum counts int8 quanta exactly
+    } else {
+        w.acc_scale = acc_scale_for(code, w.clip, w.xmin_h);
+        if (w.acc_scale == 0.0f) return;  // columns too heavy for the grid: separate pass
+        w.acc_inv = 1.0f / w.acc_scale;
+    }
+    w.acc = reinterpret_cast<int32_t *>(acc_base);
+    w.accum = 1;
 }
 
 // Floor of a heavy check output's exclusive psi sum (base-2 units). psi is
@@ -684,10 +762,14 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
                               dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
             return err;
         if (!w0.layered) {
-            const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
-            if ((err = add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0,
-                                  true)) != cudaSuccess)
-                return err;
+            if (w0.accum)
+                err = add_kernel(&n_vn, body, &n_ctrl, 1, (void *)post_kernel, post_grid(T, F), dim3(kThreads),
+                                 args, 0, true);
+            else {
+                const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
+                err = add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0, true);
+            }
+            if (err != cudaSuccess) return err;
             prev = n_vn;
             continue;
         }
@@ -769,7 +851,9 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         err = cudaLaunchKernel(cl.func, cl.grid, cl.block, args, cl.smem, stream);
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
-        if (t <= w.max_iter && !w.layered) {
+        if (t <= w.max_iter && !w.layered && w.accum) {
+            err = cudaLaunchKernel((void *)post_kernel, post_grid(T, F), dim3(kThreads), args, 0, stream);
+        } else if (t <= w.max_iter && !w.layered) {
             qc::ColsInline ccopy = code->cols_in;
             void *vn_args[] = {&tcopy, &wcopy, &ccopy};
             const VnLaunch vl = vn_launch(T, F, w.fmt, w.vn_vpt, w.vn_split);
@@ -882,6 +966,7 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
         w.ngroups = p.layers > 0 ? p.layers : T.mb;
         w.msg_buf = (int64_t)F * T.n_h * T.Z;
     }
+    set_accum(code, p, base + lo.acc, w);
 
     std::lock_guard<std::mutex> lock(code->mu);
     code->last_ws = ws;
@@ -931,7 +1016,7 @@ void destroy_graph_cache(qcldpc_code *code) {
 
 extern "C" size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
                                           const qcldpc_params *p) {
-    if (!code || n_frames < 0) return 0;
+    if (!code || n_frames < 0 || n_frames > 65535) return 0;
     const bool soft = p && p->soft_output == 1;
     const int fmt = p ? p->msg_format : 0;
     if (fmt < 0 || fmt > 2) return 0;
@@ -1135,8 +1220,12 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     qc::ColsInline ccopy = code->cols_in;
     void *vn_args[] = {&tcopy, &w, &ccopy};
     const VnLaunch vl = vn_launch(T, n_frames, w.fmt, w.vn_vpt, w.vn_split);
-    for (int r = 0; r < reps && err == cudaSuccess; r++)
-        err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
+    for (int r = 0; r < reps && err == cudaSuccess; r++) {
+        if (w.accum)
+            err = cudaLaunchKernel((void *)post_kernel, post_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+        else
+            err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
+    }
     cudaEventRecord(ev[2], stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(ev[2]);
     float a = 0.f, b = 0.f;
@@ -1204,6 +1293,11 @@ __global__ void __launch_bounds__(kThreads) pool_load_kernel(const __grid_consta
         float *row = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
         row[j] = qv;
         row[j + Z] = qv;
+        if (W.accum) {
+            int32_t *a = W.acc + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+            a[j] = 0;
+            a[j + Z] = 0;
+        }
     }
     const int lane = threadIdx.x & 31;
     const int64_t warp = tid >> 5, nwarps = nthreads >> 5;
@@ -1369,8 +1463,12 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
             err = add_kernel(&b, g, &a, 1, (void *)ctrl_kernel<false>, dim3(1), dim3(kCtrlThreads),
                              ctrl_args);
         if (!layered) {
-            if (err == cudaSuccess)
-                err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
+            if (err == cudaSuccess) {
+                if (pool->w.accum)
+                    err = add_kernel(&c, g, &b, 1, (void *)post_kernel, post_grid(T, F), dim3(kThreads), args);
+                else
+                    err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
+            }
             prev = c;
             continue;
         }
@@ -1485,6 +1583,7 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
         w.qstep = step * kLog2e;
         w.qinv = 1.0f / w.qstep;
     }
+    set_accum(code, p, base + lo.base.acc, w);
     pool->code = code;
     pool->n_slots = n_slots;
     pool_reset_kernel<<<std::max(1, std::min(1024, (n_slots + kThreads - 1) / kThreads)), kThreads, 0,
@@ -1664,7 +1763,8 @@ extern "C" int qcldpc_decode_noalloc(const qcldpc_code *code, const float *llr_d
                                      qcldpc_stream_t stream) {
     using namespace qc;
     if (!code) return fail(QCLDPC_E_INVAL, "decode_noalloc: code is NULL");
-    if (n_frames < 0) return fail(QCLDPC_E_INVAL, "decode_noalloc: negative frame count");
+    if (n_frames < 0 || n_frames > 65535)
+        return fail(QCLDPC_E_INVAL, "decode_noalloc: n_frames must be in [0, 65535]");
     const size_t need =
         layout_of(code->tab, n_frames, false, p ? p->msg_format : 0, p && p->schedule == 1).total;
     if (need > kNoallocScratchBytes)

@@ -108,7 +108,16 @@ constexpr int kTile = kCnThreads * kTmaVpt;    // checks per block, at most
 constexpr int kStage = kTile + 4;              // staged floats per row (16-byte realignment)
 constexpr int kStageWords = kTile / 32 + 4;    // staged decision words per row
 constexpr int kSmemHeader = 128;               // mbarrier, then 16-byte aligned rows
-constexpr unsigned kWaitLimit = 1u << 22;      // bounded mbarrier polls before giving up
+// Suspend-time hint of the staged check pass's barrier polls, in ns (0: none).
+#ifndef QCLDPC_WAIT_HINT_NS
+#define QCLDPC_WAIT_HINT_NS 0
+#endif
+// bounded mbarrier polls before giving up (fewer when each poll may suspend)
+#if QCLDPC_WAIT_HINT_NS > 0
+constexpr unsigned kWaitLimit = 1u << 14;
+#else
+constexpr unsigned kWaitLimit = 1u << 22;
+#endif
 // Padding elements after every workspace array: lanes and staged copies that
 // run past a row's end read here (results unused), and never past the array.
 constexpr int kSlack = 4096;
@@ -147,6 +156,17 @@ struct Work {
     int32_t lrow0, lrows;  // kPassGroup and the group's posterior update: its base rows
     int32_t cn_nt;         // check-block threads, 0 = chosen from Z (launch shape only)
     int32_t vn_vpt, vn_split;  // variable pass nodes per thread / part groups, 0 = chosen
+    // Flooding with accumulated posteriors (accum = 1): the check pass adds
+    // every new heavy message, as the integer acc_value() of its stored form,
+    // into acc at the posterior's own offset (slot 2Z + shift + i, so a
+    // column's node j collects at j and j + Z); post_kernel turns the sums
+    // into L = Q + acc_inv (acc[j] + acc[j + Z]) and clears them. Integer
+    // addition is exact and order-free: the sum, and so every posterior bit,
+    // is the same whatever order the blocks and their reductions run in.
+    int32_t *acc;          // [F][n_hcols][2Z]
+    float acc_scale;       // FP32 / FP16 messages: fixed-point scale 2^k (int8: unused)
+    float acc_inv;         // 2^-k, or the int8 quantum (the sum then counts quanta)
+    int32_t accum;         // 1: accumulated posteriors; 0: separate summing variable pass
 };
 // Kinds of check pass. kPassFlood: flooding iteration t (stop test of t-1
 // when due, then the update). kPassTest: the stop test of iteration t-1
@@ -307,6 +327,20 @@ struct Codec<int8_t> {
         return (int8_t)__float2int_rn(fminf(fmaxf(v * W.qinv, -127.0f), 127.0f));
     }
 };
+
+// The integer a stored message adds to its node's accumulator: the stored
+// value in units of acc_inv (the int8 code itself; FP32 and FP16 values
+// rounded to the fixed-point grid 2^-k).
+__device__ __forceinline__ int acc_value(float v, const Work &W) { return __float2int_rn(v * W.acc_scale); }
+__device__ __forceinline__ int acc_value(__half v, const Work &W) {
+    return __float2int_rn(__half2float(v) * W.acc_scale);
+}
+__device__ __forceinline__ int acc_value(int8_t v, const Work &) { return (int)v; }
+
+// Reduction into an accumulator (no return value: the add runs in L2).
+__device__ __forceinline__ void red_add(int32_t *p, int v) {
+    asm volatile("red.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 }  // namespace
 

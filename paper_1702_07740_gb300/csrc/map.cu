@@ -1,6 +1,6 @@
 // Syndrome and 8-dimensional reconciliation kernels.
 //
-// * qcldpc_syndrome: s = H x over GF(2) for the QC expansion of Sec. III-D,
+// * qcldpc_syndrome: s = H x over GF(2) for the QC expansion of Sec. III-C,
 //   one thread per check node, results packed with a warp ballot.
 // * qcldpc_bob_message_8d / qcldpc_llr_8d: Sec. II-C. Bob sends M = U Y with
 //   U_j = (-1)^{C_j}; Alice divides, R = M X^{-1} = M conj(X) / |X|^2, and

@@ -132,7 +132,7 @@ struct qcldpc_code {
     void *last_ws;      // workspace, frame count and soft flag of the last decode
     int last_frames;
     int last_soft;
-    unsigned char last_work[256];  // the last decode's kernel arguments (decode.cu)
+    unsigned char last_work[320];  // the last decode's kernel arguments (decode.cu)
 };
 
 namespace qc {

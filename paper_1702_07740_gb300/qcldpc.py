@@ -56,6 +56,7 @@ class qcldpc_params(ctypes.Structure):
         ("cn_threads", ctypes.c_int32),
         ("vn_nodes", ctypes.c_int32),
         ("vn_split", ctypes.c_int32),
+        ("vn_pass", ctypes.c_int32),
     ]
 
 

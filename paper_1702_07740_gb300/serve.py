@@ -33,6 +33,7 @@ class Request:
     syn: torch.Tensor        # device int32[ceil(m/32)]
     tag: object = None
     t_arrival: float = field(default_factory=time.perf_counter)
+    ready: torch.cuda.Event | None = None  # set by submit: the buffers' writes are done
 
 
 @dataclass
@@ -76,6 +77,11 @@ class Server:
                               torch.empty(s, dtype=torch.int32, device="cuda"))
 
     def submit(self, req: Request):
+        """Queue a request. Its buffers may still be being written on the
+        caller's current stream: an event recorded there now orders the
+        server's load of them after those writes."""
+        req.ready = torch.cuda.Event()
+        req.ready.record(torch.cuda.current_stream())
         self.queue[req.code].append(req)
 
     def pending(self) -> int:
@@ -87,6 +93,8 @@ class Server:
             while self.queue[name] and self.free[name]:
                 req = self.queue[name].popleft()
                 s = self.free[name].popleft()
+                if req.ready is not None:
+                    self.stream.wait_event(req.ready)
                 q.qcldpc_pool_load(pool, 1, ids[s:s + 1], req.llr, req.syn, self.stream)
                 self.busy[name][s] = req
         names = [name for name in self.pools if self.busy[name]]

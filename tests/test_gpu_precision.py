@@ -1,15 +1,20 @@
 """Low-precision message storage (FP16, scaled int8) against the FP64 oracle.
 
 All arithmetic stays FP32; only the stored check-to-variable messages change.
-The error bars asserted here are measured properties of each format, stated
-next to the FP32 bar of test_gpu_parity (1e-3 relative):
+What each format is held to:
 * FP16: every message is rounded to 11 significant bits; the rounding
   compounds through the iterations, and posteriors after 50 iterations at
   SNR 0.029 stay within 5e-2 relative (scaled as in test_gpu_parity;
   measured over 20 frames: max 3.7e-2, p99.9 2.0e-2, median 2.3e-4);
 * int8 with quantum d: after one iteration each of a node's messages is off
-  by at most d/2, so |L_gpu - L_ref| <= deg(v) d / 2 (+ FP32 slack); after 50
-  iterations the error has compounded (median 0.1 scaled, see the test).
+  by at most d/2, so |L_gpu - L_ref| <= deg(v) d / 2 (+ FP32 slack), asserted.
+  No bound of that kind survives many iterations: the check rule is
+  1-Lipschitz in each input, but a variable node passes on the sum of up to
+  deg(v) - 1 perturbed messages, so the worst-case growth per iteration is
+  (deg(v) - 1)(deg(c) - 1), about 140 for these codes. After 50 iterations
+  the test therefore asserts the decoding outcome instead: on frames that
+  both the int8 decoder and the oracle converge on, the key bits are the
+  oracle's. The 50-iteration error at SNR 0.029 is printed, not asserted.
 """
 import numpy as np
 import pytest
@@ -77,23 +82,35 @@ def test_fp16_posteriors_after_50_iterations(twenty_frames):
     assert err.max() <= 5e-2
 
 
-def test_int8_posteriors_after_50_iterations(twenty_frames):
-    """int8 with the default quantum (clip / 127 = 0.118): the quantisation
-    error compounds over the iterations of a frame that does not converge.
-    Measured over 20 frames: median scaled error 0.105, p99.9 10.3 (absolute
-    errors up to ~2 on posteriors near zero, where the scale floor is 0.1),
-    3.4 % of posterior signs differ from the oracle's. The bounds below hold
-    these measured levels with margin."""
+def test_int8_posteriors_after_50_iterations_are_reported(twenty_frames):
+    """int8 with the default quantum (clip / 127 = 0.118) at SNR 0.029, where
+    no frame converges: the error against the oracle after 50 iterations is
+    printed (no bound holds there, see the module docstring); the posteriors
+    must be finite."""
     fr, refs = twenty_frames
     code = q.create_code_from(fr.code_dict)
     _, _, _, post = _decode(code, fr, _llr(fr), 50, fmt=2, et_start=51)
+    assert np.isfinite(post).all()
     err = _scaled_err(post, refs)
     flips = np.mean(np.sign(post) != np.sign(refs))
     print(f"int8, 20 frames: max scaled err {err.max():.2e}, p99.9 {np.quantile(err, 0.999):.2e}, "
           f"median {np.median(err):.2e}, sign disagreement {flips:.2e}")
-    assert np.median(err) <= 0.2
-    assert np.quantile(err, 0.999) <= 20.0
-    assert flips <= 0.05
+
+
+def test_int8_keys_equal_the_oracle_on_frames_both_converge():
+    """At SNR 0.2 (Z = 2000) frames converge: on every frame that the int8
+    decoder and the FP64 oracle both converge on, the key bits agree."""
+    fr = make_frames(synth.rate002_code(2000), 0.2, 6)
+    code = q.create_code_from(fr.code_dict)
+    k8, c8, i8, _ = _decode(code, fr, _llr(fr), 100, fmt=2)
+    both = 0
+    for f in range(fr.F):
+        _, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], 100)
+        if c8[f] and cv:
+            both += 1
+            np.testing.assert_array_equal(k8[f], chat[: fr.code.k], f"frame {f}")
+    print(f"int8, SNR 0.2: {both} of {fr.F} frames converged on both sides")
+    assert both >= 3
 
 
 @pytest.mark.parametrize("step", [0.05, 0.118])
