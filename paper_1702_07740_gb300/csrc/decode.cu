@@ -322,6 +322,9 @@ __global__ void __launch_bounds__(kThreads) vn_kernel(const __grid_constant__ Ta
 // have just reduced into took more than twice as long (18 us against 7.5 us
 // for 16 frames of the n = 10^6 code, measured in isolation).
 constexpr int kPostVpt = 2;
+// PAIR (even Z): a thread takes adjacent nodes j, j + 1 (j even) with one
+// 64-bit exchange per accumulator half, and vector loads and stores.
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads) post_kernel(const __grid_constant__ Table T,
                                                         const __grid_constant__ Work W) {
     pdl_wait();  // the control step's flags (and the check pass's sums) are complete and visible
@@ -333,10 +336,25 @@ __global__ void __launch_bounds__(kThreads) post_kernel(const __grid_constant__ 
     const float *__restrict__ q = W.llr + (size_t)f * W.n + (size_t)T.hcol_base[hc] * Z;
     float *__restrict__ L = W.L + ((size_t)f * T.n_hcols + hc) * 2 * Z;
     int32_t *__restrict__ a = W.acc + ((size_t)f * T.n_hcols + hc) * 2 * Z;
+    constexpr int P = PAIR ? 2 : 1;  // nodes per exchange
 #pragma unroll
     for (int u = 0; u < kPostVpt; u++) {
-        const int j = (blockIdx.x * kPostVpt + u) * kThreads + threadIdx.x;
-        if (j < Z) {
+        const int j = P * ((blockIdx.x * kPostVpt + u) * kThreads + threadIdx.x);
+        if (j >= Z) continue;
+        if constexpr (PAIR) {
+            // exchanges of the 8-byte words (a[j], a[j+1]) and (a[j+Z], a[j+Z+1])
+            unsigned long long *a2 = reinterpret_cast<unsigned long long *>(a + j);
+            unsigned long long *b2 = reinterpret_cast<unsigned long long *>(a + j + Z);
+            const unsigned long long x = atomicExch(a2, 0ull), y = atomicExch(b2, 0ull);
+            const int s0 = (int)(uint32_t)x + (int)(uint32_t)y;
+            const int s1 = (int)(uint32_t)(x >> 32) + (int)(uint32_t)(y >> 32);
+            const float2 qq = __ldg(reinterpret_cast<const float2 *>(q + j));
+            float2 lv;
+            lv.x = fmaf((float)s0, W.acc_inv, qq.x * kLog2e) + 0.0f;  // -0 -> +0
+            lv.y = fmaf((float)s1, W.acc_inv, qq.y * kLog2e) + 0.0f;
+            *reinterpret_cast<float2 *>(L + j) = lv;
+            *reinterpret_cast<float2 *>(L + j + Z) = lv;
+        } else {
             const int sum = atomicExch(a + j, 0) + atomicExch(a + j + Z, 0);
             const float lvj = fmaf((float)sum, W.acc_inv, __ldg(q + j) * kLog2e) + 0.0f;  // -0 -> +0
             L[j] = lvj;
@@ -345,8 +363,12 @@ __global__ void __launch_bounds__(kThreads) post_kernel(const __grid_constant__ 
     }
 }
 
+// The accumulated-posterior variable pass for a code: kernel and grid.
+void *post_func(const Table &T) {
+    return T.Z % 2 == 0 ? (void *)post_kernel<true> : (void *)post_kernel<false>;
+}
 dim3 post_grid(const Table &T, int F) {
-    const int span = kThreads * kPostVpt;
+    const int span = kThreads * kPostVpt * (T.Z % 2 == 0 ? 2 : 1);
     return dim3((unsigned)((T.Z + span - 1) / span), (unsigned)(T.n_hcols > 0 ? T.n_hcols : 1), (unsigned)F);
 }
 
@@ -763,7 +785,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
             return err;
         if (!w0.layered) {
             if (w0.accum)
-                err = add_kernel(&n_vn, body, &n_ctrl, 1, (void *)post_kernel, post_grid(T, F), dim3(kThreads),
+                err = add_kernel(&n_vn, body, &n_ctrl, 1, post_func(T), post_grid(T, F), dim3(kThreads),
                                  args, 0, true);
             else {
                 const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
@@ -852,7 +874,7 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
         if (err != cudaSuccess) break;
         ctrl_kernel<false><<<1, kCtrlThreads, 0, stream>>>(w, none);
         if (t <= w.max_iter && !w.layered && w.accum) {
-            err = cudaLaunchKernel((void *)post_kernel, post_grid(T, F), dim3(kThreads), args, 0, stream);
+            err = cudaLaunchKernel(post_func(T), post_grid(T, F), dim3(kThreads), args, 0, stream);
         } else if (t <= w.max_iter && !w.layered) {
             qc::ColsInline ccopy = code->cols_in;
             void *vn_args[] = {&tcopy, &wcopy, &ccopy};
@@ -1222,7 +1244,7 @@ extern "C" int qcldpc_time_passes(const qcldpc_code *code_c, int n_frames, void 
     const VnLaunch vl = vn_launch(T, n_frames, w.fmt, w.vn_vpt, w.vn_split);
     for (int r = 0; r < reps && err == cudaSuccess; r++) {
         if (w.accum)
-            err = cudaLaunchKernel((void *)post_kernel, post_grid(T, n_frames), dim3(kThreads), args, 0, stream);
+            err = cudaLaunchKernel(post_func(T), post_grid(T, n_frames), dim3(kThreads), args, 0, stream);
         else
             err = cudaLaunchKernel(vl.func, vl.grid, dim3(kThreads), vn_args, 0, stream);
     }
@@ -1465,7 +1487,7 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
         if (!layered) {
             if (err == cudaSuccess) {
                 if (pool->w.accum)
-                    err = add_kernel(&c, g, &b, 1, (void *)post_kernel, post_grid(T, F), dim3(kThreads), args);
+                    err = add_kernel(&c, g, &b, 1, post_func(T), post_grid(T, F), dim3(kThreads), args);
                 else
                     err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
             }
