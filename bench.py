@@ -82,6 +82,8 @@ def parse_args():
     ap.add_argument("--mix-snrs", default="0.16,0.5,1.0",
                     help="batch/serve: SNR of the rate 0.02 / 0.05 / 0.10 codes (every length)")
     ap.add_argument("--mix-frames", type=int, default=256, help="batch: frames in the mix")
+    ap.add_argument("--mix-reps", type=int, default=20,
+                    help="batch: timed decodes of the mix per variant (their mean is reported)")
     ap.add_argument("--loads", default="0.1,0.2,0.3,0.4,0.5,0.6,0.7,0.8,0.9,1.0,1.1,1.2",
                     help="serve: offered load as a fraction of the measured batched capacity")
     ap.add_argument("--serve-requests", type=int, default=2000,

@@ -6,9 +6,11 @@
   with its Wilson 95 % interval, the paired difference to FP32 with its 95 %
   interval, mean iterations and decoded Mbit/s.
 * ``batch``: 256 frames drawn uniformly from nine codes (rates 0.02, 0.05
-  and 0.10, each at n = 10^5, 4*10^5 and 10^6) decoded together by frame
-  pools stepped in one graph launch (FP16 and FP32 messages), against the
-  plain FP32 decoder run one frame at a time and one code at a time.
+  and 0.10, each at n = 10^5, 4*10^5 and 10^6) decoded together in one
+  batched decode (one graph launch with a device-side loop over all codes),
+  and by frame pools stepped in one graph launch per step (FP16 and FP32
+  messages), against the plain FP32 decoder run one frame at a time and one
+  code at a time. Each variant decodes the mix --mix-reps times in a row.
 * ``schedule``: the library's autotuner (flooding vs layered with 2, 7 and
   mb row groups) on a 16-frame sample of each FER operating point.
 * ``et``: delayed early termination, an SNR -> et_start table built from
@@ -254,6 +256,30 @@ class PerFrame:
         return time.perf_counter() - t0, res
 
 
+class MultiBatch:
+    """Every frame of the mix in one batched decode (qcldpc_decode_multi):
+    one graph launch runs all codes' passes side by side until every frame
+    stopped."""
+
+    def __init__(self, codes, counts, fmt):
+        self.codes, self.counts = codes, counts
+        self.names = list(codes)
+        self.dec = q.MultiDecoder([codes[c] for c in self.names], [counts[c] for c in self.names],
+                                  q.qcldpc_params_init(msg_format=FMT[fmt]))
+
+    def run(self, inputs, max_iter):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        self.dec.decode([inputs[c][0] for c in self.names], [inputs[c][1] for c in self.names], max_iter)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res = {}
+        for i, c in enumerate(self.names):
+            wk, F = (self.codes[c].k + 31) // 32, self.counts[c]
+            res[c] = (self.dec.keys[i][: F * wk].view(F, wk), self.dec.converged[i][:F], self.dec.iters[i][:F])
+        return dt, res
+
+
 class PerCode:
     """The plain FP32 decoder, one call per code with all of its frames."""
 
@@ -282,11 +308,15 @@ def summarise(codes, inputs, counts, sec, res):
     for c in codes:
         keys, conv, its = res[c]
         e = (keys != inputs[c][2]).any(1).cpu().numpy().astype(np.int64)
+        cv = conv.cpu().numpy() == 1
         err_all.append(e)
         bits += counts[c] * codes[c].n
         info += int((e == 0).sum()) * codes[c].k
+        # undetected: the decoder stopped on a codeword of the coset that is
+        # not Bob's (H C = s holds, the key differs); detected: no convergence
         per[c] = {"frames": counts[c], "errors": int(e.sum()),
-                  "converged": int((conv.cpu().numpy() == 1).sum()),
+                  "undetected": int((cv & (e == 1)).sum()), "detected": int((~cv & (e == 1)).sum()),
+                  "converged": int(cv.sum()),
                   "mean_iters": float(its.float().mean().item()),
                   "max_iters": int(its.max().item())}
     e = np.concatenate(err_all)
@@ -301,8 +331,11 @@ def study_batch(args):
     codes, inputs, snrs = mix_setup(args, counts)
     pb16 = PoolBatch(codes, counts, "fp16", args.max_iter)
     pb32 = PoolBatch(codes, counts, "fp32", args.max_iter)
+    mb16, mb32 = MultiBatch(codes, counts, "fp16"), MultiBatch(codes, counts, "fp32")
     per_frame, per_code = PerFrame(codes), PerCode(codes, counts)
     runs = {
+        "multi_fp16": lambda: mb16.run(inputs, args.max_iter),
+        "multi_fp32": lambda: mb32.run(inputs, args.max_iter),
         "pools_fp16": lambda: pb16.run(inputs),
         "pools_fp32": lambda: pb32.run(inputs),
         "per_frame_fp32": lambda: per_frame.run(inputs, counts, args.max_iter),
@@ -314,13 +347,24 @@ def study_batch(args):
                    for name, _, Z, _ in MIX if name in codes},
            "runs": {}}
     errs = {}
+    reps = args.mix_reps
+    out["reps_per_run"] = reps
     for key, fn in runs.items():
         fn()  # warm-up: graphs instantiated, workspaces touched
-        sec, res = fn()
-        out["runs"][key], errs[key] = summarise(codes, inputs, counts, sec, res)
+        total = 0.0
+        for _ in range(reps):  # the same frames again: a timed region of reps decodes of the mix
+            sec, res = fn()
+            total += sec
+        out["runs"][key], errs[key] = summarise(codes, inputs, counts, total / reps, res)
+        out["runs"][key]["timed_seconds"] = total
     for key in runs:
         if key != "per_frame_fp32":
             out["runs"][key]["vs_per_frame_fp32"] = paired(errs["per_frame_fp32"], errs[key])
+        if key != "per_code_fp32":
+            out["runs"][key]["vs_per_code_fp32"] = paired(errs["per_code_fp32"], errs[key])
+    for key in ("multi_fp16", "pools_fp16"):
+        out[f"speedup_{key}_vs_per_code_fp32"] = (out["runs"][key]["mbps"]
+                                                   / out["runs"]["per_code_fp32"]["mbps"])
     out["speedup_pools_fp16_vs_per_frame_fp32"] = (out["runs"]["pools_fp16"]["mbps"]
                                                    / out["runs"]["per_frame_fp32"]["mbps"])
     emit(out)
@@ -331,7 +375,8 @@ def study_batch(args):
 def serve_once(srv, codes, bank, arrivals, passes):
     """Real-time run of the continuous-batching server on one arrival trace
     (the server is idle before and after). arrivals: list of (t_offset_s,
-    code, frame index)."""
+    code, frame index). Returns latencies, per-request key errors, the run's
+    seconds and the number of errors on converged frames (undetected)."""
     results = []
     t0 = time.perf_counter()
     i, N = 0, len(arrivals)
@@ -351,9 +396,10 @@ def serve_once(srv, codes, bank, arrivals, passes):
     t_end = time.perf_counter()
     lat = np.array([r.latency for r in results])
     keys_h = {c: bank[c][2].cpu() for c in codes}
-    err = np.array([int((r.keys != keys_h[r.code][r.tag[2]]).any())
-                    for r in sorted(results, key=lambda r: r.tag[0])])
-    return lat, err, t_end - t0
+    ordered = sorted(results, key=lambda r: r.tag[0])
+    err = np.array([int((r.keys != keys_h[r.code][r.tag[2]]).any()) for r in ordered])
+    undetected = int(sum(1 for r, e in zip(ordered, err) if e and r.converged == 1))
+    return lat, err, t_end - t0, undetected
 
 
 def fifo_once(per_frame, bank, max_iter, arrivals):
@@ -387,6 +433,7 @@ def study_serve(args):
     names = [name for name, _, _, _ in MIX]
     params = q.qcldpc_params_init(msg_format=FMT["fp16"])
     slots = {name: 32 for name in names}
+    chunk = 16
     passes = 4
     budget = 64 << 30
     bits = {c: codes[c].n for c in names}
@@ -394,9 +441,10 @@ def study_serve(args):
     rng = np.random.default_rng(12345)
     burst = [(0.0, names[j % len(names)], int(rng.integers(0, n_bank)))
              for j in range(len(names) * 64)]
-    srv = serve.Server(codes, slots, args.max_iter, params, hbm_budget_bytes=budget)
+    srv = serve.Server(codes, args.max_iter, params, hbm_budget_bytes=budget, chunk_slots=chunk,
+                       slots=slots)
     serve_once(srv, codes, bank, burst[:30], passes)  # warm-up: graphs instantiated
-    lat, err, sec = serve_once(srv, codes, bank, burst, passes)
+    lat, err, sec, _ = serve_once(srv, codes, bank, burst, passes)
     footprint = srv.footprint
     cap_fps = len(burst) / sec
     per_frame = PerFrame(codes)
@@ -404,19 +452,21 @@ def study_serve(args):
     emit({"study": "serve", "phase": "capacity", "frames": len(burst), "seconds": sec,
           "frames_per_s": cap_fps,
           "mbps": sum(bits[c] for _, c, _ in burst) / sec / 1e6,
-          "slots": slots, "passes_per_tick": passes, "msg_format": "fp16",
+          "slots_up_front": slots, "chunk_slots": chunk, "slots_after": srv.slots(),
+          "peak_footprint_bytes": srv.peak_used, "passes_per_tick": passes, "msg_format": "fp16",
           "device_footprint_bytes": footprint,
           "mix": {name: {"n": codes[name].n, "snr": snrs[name]} for name in names}})
     for li, load in enumerate(parse_floats(args.loads)):
         arr = trace(np.random.default_rng(1000 + li), load * cap_fps, args.serve_requests, n_bank,
                     names)
-        lat, err, sec = serve_once(srv, codes, bank, arr, passes)
+        lat, err, sec, undet = serve_once(srv, codes, bank, arr, passes)
         flat, ferr, fsec = fifo_once(per_frame, bank, args.max_iter, arr)
         total_bits = sum(bits[c] for _, c, _ in arr)
         emit({"study": "serve", "load": load, "offered_fps": load * cap_fps, "requests": len(arr),
               "server": {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
                          "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                         "mbps": total_bits / sec / 1e6, **fer_entry(err)},
+                         "mbps": total_bits / sec / 1e6, **fer_entry(err),
+                         "undetected": undet},
               "per_frame_fifo_fp32": {"p50_ms": 1e3 * float(np.percentile(flat, 50)),
                                       "p99_ms": 1e3 * float(np.percentile(flat, 99)),
                                       "mbps": total_bits / fsec / 1e6, **fer_entry(ferr)},

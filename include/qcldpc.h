@@ -260,6 +260,40 @@ int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
                        size_t workspace_bytes, qcldpc_stream_t stream);
 
 /*
+ * Batched decoding of the frames of several codes in one graph launch (frame
+ * batching across codes; the paper decodes one frame of one code per GPU).
+ * Code c's n_frames[c] frames run the rule of qcldpc_decode (flooding,
+ * Algorithm 1) with their own stop test; one device-side loop runs the
+ * passes of all codes side by side until every frame has stopped. The
+ * results (key bits, flags, iterations) are the ones one qcldpc_decode call
+ * per code with the same frames and options returns.
+ *
+ *   n_codes         1..QCLDPC_MULTI_MAX_CODES
+ *   codes           HOST array of n_codes code handles (distinct or not)
+ *   llr_dev, syn_dev, key_bits_dev, converged_dev, iters_dev
+ *                   HOST arrays of n_codes DEVICE pointers, each laid out
+ *                   as for qcldpc_decode with that code and frame count
+ *                   (LLRs 16-byte aligned); entries of codes with no frame
+ *                   may be NULL
+ *   n_frames        HOST int[n_codes], each 0..65535
+ *   p               options as for qcldpc_decode; schedule must be 0
+ *                   (flooding) and soft_output 0
+ *   workspace_dev   DEVICE scratch of qcldpc_decode_multi_workspace() bytes,
+ *                   256-byte aligned
+ * Enqueues on `stream`; the instantiated graph is cached per argument set.
+ * Errors: QCLDPC_E_INVAL, _ALIGN, _NOMEM (workspace too small), _CUDA.
+ */
+#define QCLDPC_MULTI_MAX_CODES 16
+size_t qcldpc_decode_multi_workspace(int n_codes, const qcldpc_code *const *codes,
+                                     const int *n_frames, const qcldpc_params *p);
+int qcldpc_decode_multi(int n_codes, const qcldpc_code *const *codes,
+                        const float *const *llr_dev, const uint32_t *const *syn_dev,
+                        const int *n_frames, int max_iter, const qcldpc_params *p,
+                        uint32_t *const *key_bits_dev, int32_t *const *converged_dev,
+                        int32_t *const *iters_dev, void *workspace_dev,
+                        size_t workspace_bytes, qcldpc_stream_t stream);
+
+/*
  * Pools: continuous batching of frames of one code (serving). A pool is a
  * fixed set of n_slots frame slots with all decoder state in one caller-owned
  * workspace (qcldpc_pool_workspace bytes, 256-byte aligned). Frames are loaded

@@ -387,6 +387,7 @@ extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,
 extern "C" void qcldpc_destroy_code(qcldpc_code *code) {
     if (!code) return;
     qc::destroy_graph_cache(code);
+    qc::purge_multi_graphs(code);
     qc::release_tables(code);
     delete code;
 }

@@ -755,8 +755,12 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
 // Loop body of the decode graph. Flooding: check pass -> control ->
 // variable pass. Layered: stop-test pass -> control -> for every row group,
 // its check pass -> its posterior update.
+// set_cond: the body's control steps set the loop condition from this
+// code's frames (a one-code decode); otherwise the caller adds a step that
+// sets it. *last (if given) receives the body's last node.
 cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline &CI,
-                          const Work &w0, cudaGraphConditionalHandle handle) {
+                          const Work &w0, cudaGraphConditionalHandle handle, bool set_cond = true,
+                          cudaGraphNode_t *last = nullptr) {
     const int F = w0.n_frames;
     Table tcopy = T;
     Work wcopy = w0;
@@ -780,7 +784,8 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
         if ((err = add_kernel(&n_cn, body, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
                               args, cl.smem, prev != nullptr && QCLDPC_PDL_LOOP)) != cudaSuccess)
             return err;
-        if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
+        if ((err = add_kernel(&n_ctrl, body, &n_cn, 1,
+                              set_cond ? (void *)ctrl_kernel<true> : (void *)ctrl_kernel<false>, dim3(1),
                               dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
             return err;
         if (!w0.layered) {
@@ -813,6 +818,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
             prev = b;
         }
     }
+    if (last) *last = prev;
     return cudaSuccess;
 }
 
@@ -905,44 +911,14 @@ int stream_decode(qcldpc_code *code, const Work &w, cudaStream_t stream) {
     return QCLDPC_OK;
 }
 
-int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn, int F,
-                int max_iter, const qcldpc_params *p_in, uint32_t *keys, int32_t *conv,
-                int32_t *iters, float *post, void *ws, size_t ws_bytes, cudaStream_t stream) {
-    using namespace qc;
-    qcldpc_code *code = const_cast<qcldpc_code *>(code_c);
-    if (!code) return fail(QCLDPC_E_INVAL, "decode: code is NULL");
-    qcldpc_params p;
-    if (p_in) p = *p_in;
-    else qcldpc_params_init(&p);
-    const bool soft = post != nullptr;
-    if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode: n_frames must be in [0, 65535]");
-    if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
-    if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
-        p.msg_format > 2 || !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1) ||
-        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)) || !shape_ok(p))
-        return fail(QCLDPC_E_INVAL,
-                    "decode: unsupported option (phi_floor > 0, schedule 0..1, layers 0..mb, "
-                    "msg_format 0..2, msg_step >= 0, launch shapes)");
-    if (soft && p.soft_output != 1)
-        return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
-    if (F == 0) return QCLDPC_OK;
-    if (!llr || !syn || !keys || !conv || !iters || !ws)
-        return fail(QCLDPC_E_INVAL, "decode: NULL buffer");
-    if (!aligned(ws, 256)) return fail(QCLDPC_E_ALIGN, "decode: workspace must be 256-byte aligned");
-    if (!aligned(llr, 4) || !aligned(syn, 4) || !aligned(keys, 4) || !aligned(conv, 4) ||
-        !aligned(iters, 4) || (post && !aligned(post, 4)))
-        return fail(QCLDPC_E_ALIGN, "decode: buffers must be 4-byte aligned");
-    int dev = -1;
-    cudaError_t err = cudaGetDevice(&dev);
-    if (err != cudaSuccess) return cuda_fail(err, "decode: cudaGetDevice");
-    if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode: current device differs from the code's device");
-
-    if (int st = upload_tables(code)) return st;
+// The kernels' argument block for one decode call of `code` on F frames
+// whose workspace starts at base with layout lo (options p already checked).
+Work make_work(const qcldpc_code *code, const qcldpc_params &p, int F, int max_iter, const float *llr,
+               const uint32_t *syn, uint32_t *keys, int32_t *conv, int32_t *iters, float *post,
+               char *base, const Layout &lo) {
     const Table &T = code->tab;
+    const bool soft = post != nullptr;
     const bool layered = p.schedule == 1;
-    const Layout lo = layout_of(T, F, soft, p.msg_format, layered);
-    if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
-    char *base = static_cast<char *>(ws);
     Work w;
     std::memset(&w, 0, sizeof(w));  // padding bytes take part in cache keys
     w.llr = llr;
@@ -989,6 +965,47 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
         w.msg_buf = (int64_t)F * T.n_h * T.Z;
     }
     set_accum(code, p, base + lo.acc, w);
+    return w;
+}
+
+int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn, int F,
+                int max_iter, const qcldpc_params *p_in, uint32_t *keys, int32_t *conv,
+                int32_t *iters, float *post, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    using namespace qc;
+    qcldpc_code *code = const_cast<qcldpc_code *>(code_c);
+    if (!code) return fail(QCLDPC_E_INVAL, "decode: code is NULL");
+    qcldpc_params p;
+    if (p_in) p = *p_in;
+    else qcldpc_params_init(&p);
+    const bool soft = post != nullptr;
+    if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode: n_frames must be in [0, 65535]");
+    if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
+    if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
+        p.msg_format > 2 || !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1) ||
+        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)) || !shape_ok(p))
+        return fail(QCLDPC_E_INVAL,
+                    "decode: unsupported option (phi_floor > 0, schedule 0..1, layers 0..mb, "
+                    "msg_format 0..2, msg_step >= 0, launch shapes)");
+    if (soft && p.soft_output != 1)
+        return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
+    if (F == 0) return QCLDPC_OK;
+    if (!llr || !syn || !keys || !conv || !iters || !ws)
+        return fail(QCLDPC_E_INVAL, "decode: NULL buffer");
+    if (!aligned(ws, 256)) return fail(QCLDPC_E_ALIGN, "decode: workspace must be 256-byte aligned");
+    if (!aligned(llr, 4) || !aligned(syn, 4) || !aligned(keys, 4) || !aligned(conv, 4) ||
+        !aligned(iters, 4) || (post && !aligned(post, 4)))
+        return fail(QCLDPC_E_ALIGN, "decode: buffers must be 4-byte aligned");
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "decode: cudaGetDevice");
+    if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode: current device differs from the code's device");
+
+    if (int st = upload_tables(code)) return st;
+    const Table &T = code->tab;
+    const bool layered = p.schedule == 1;
+    const Layout lo = layout_of(T, F, soft, p.msg_format, layered);
+    if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
+    Work w = make_work(code, p, F, max_iter, llr, syn, keys, conv, iters, post, static_cast<char *>(ws), lo);
 
     std::lock_guard<std::mutex> lock(code->mu);
     code->last_ws = ws;
@@ -1065,6 +1082,223 @@ extern "C" int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
     return decode_impl(code, llr_dev, syn_dev, n_frames, max_iter, p, key_bits_dev,
                        converged_dev, iters_dev, posterior_dev, workspace_dev, workspace_bytes,
                        (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Batched decoding: the frames of several codes in one graph launch.
+//
+// The graph initialises every code's frames, then runs one device-side loop
+// (a conditional WHILE node) whose body holds, for every code, the same
+// chain of flooding passes a one-code decode runs (check pass, control step,
+// posterior pass, kLoopUnroll times), side by side, so the small grids of
+// short codes fill the GPU together; a last step of the body keeps the loop
+// running while any frame of any code is active. Each frame keeps its own
+// iteration counter and stop test, so its result is the one a one-code
+// decode of the same frames gives.
+namespace {
+
+constexpr int kMultiMaxCodes = QCLDPC_MULTI_MAX_CODES;
+
+struct MultiActive {
+    int32_t n;
+    int32_t frames[kMultiMaxCodes];
+    const int32_t *active[kMultiMaxCodes];
+};
+
+__global__ void __launch_bounds__(kCtrlThreads) multi_cond_kernel(const __grid_constant__ MultiActive A,
+                                                                  cudaGraphConditionalHandle handle) {
+    __shared__ int any;
+    if (threadIdx.x == 0) any = 0;
+    __syncthreads();
+    for (int c = 0; c < A.n; c++)
+        for (int f = threadIdx.x; f < A.frames[c]; f += blockDim.x)
+            if (A.active[c][f]) any = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
+}
+
+struct MultiDecodeGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<const qcldpc_code *> codes;
+    std::vector<Work> works;
+    unsigned long long stamp = 0;
+};
+constexpr int kMultiDecodeGraphs = 8;
+std::mutex g_mdec_mu;
+MultiDecodeGraph g_mdec[kMultiDecodeGraphs];
+unsigned long long g_mdec_clock = 0;
+
+void free_multi(MultiDecodeGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+    g.codes.clear();
+    g.works.clear();
+}
+
+int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code *> &codes,
+                      const std::vector<Work> &works) {
+    cudaError_t err;
+    cudaGraph_t g = nullptr;
+    if ((err = cudaGraphCreate(&g, 0)) != cudaSuccess) return qc::cuda_fail(err, "decode_multi: cudaGraphCreate");
+    ge.graph = g;
+    const int blocks = sm_count() * 4;
+    const int n = (int)codes.size();
+    std::vector<cudaGraphNode_t> inits(n), lasts(n);
+    for (int c = 0; c < n; c++) {
+        Table tcopy = codes[c]->tab;
+        Work wcopy = works[c];
+        void *args[] = {&tcopy, &wcopy};
+        if ((err = add_kernel(&inits[c], g, nullptr, 0, (void *)init_kernel, dim3(blocks), dim3(kThreads),
+                              args)) != cudaSuccess)
+            return qc::cuda_fail(err, "decode_multi: add init node");
+    }
+    cudaGraphConditionalHandle handle;
+    if ((err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return qc::cuda_fail(err, "decode_multi: cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t n_cond;
+    if ((err = cudaGraphAddNode(&n_cond, g, inits.data(), nullptr, n, &cp)) != cudaSuccess)
+        return qc::cuda_fail(err, "decode_multi: add conditional node");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MultiActive A;
+    std::memset(&A, 0, sizeof(A));
+    A.n = n;
+    for (int c = 0; c < n; c++) {
+        if ((err = add_loop_body(body, codes[c]->tab, codes[c]->cols_in, works[c], handle, false, &lasts[c])) !=
+            cudaSuccess)
+            return qc::cuda_fail(err, "decode_multi: add loop body");
+        A.frames[c] = works[c].n_frames;
+        A.active[c] = works[c].active;
+    }
+    cudaGraphNode_t n_join;
+    void *jargs[] = {&A, &handle};
+    if ((err = add_kernel(&n_join, body, lasts.data(), n, (void *)multi_cond_kernel, dim3(1), dim3(kCtrlThreads),
+                          jargs)) != cudaSuccess)
+        return qc::cuda_fail(err, "decode_multi: add loop condition");
+    for (int c = 0; c < n; c++) {
+        Table tcopy = codes[c]->tab;
+        Work wcopy = works[c];
+        void *args[] = {&tcopy, &wcopy};
+        cudaGraphNode_t n_final;
+        if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks), dim3(kThreads),
+                              args)) != cudaSuccess)
+            return qc::cuda_fail(err, "decode_multi: add output kernel");
+    }
+    cudaGraphExec_t exec = nullptr;
+    if ((err = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess)
+        return qc::cuda_fail(err, "decode_multi: cudaGraphInstantiate");
+    ge.exec = exec;
+    ge.codes = codes;
+    ge.works = works;
+    return QCLDPC_OK;
+}
+
+// Validated options of a batched decode (flooding, hard output, FP32 / FP16 /
+// int8 storage, launch shapes chosen by the library per code).
+bool multi_params_ok(const qcldpc_params &p) {
+    return p.phi_floor > 0.0f && p.schedule == 0 && p.soft_output == 0 && p.msg_format >= 0 &&
+           p.msg_format <= 2 && p.msg_step >= 0.0f && shape_ok(p);
+}
+
+}  // namespace
+
+namespace qc {
+void purge_multi_graphs(const qcldpc_code *code) {
+    std::lock_guard<std::mutex> lock(g_mdec_mu);
+    for (auto &g : g_mdec)
+        if (g.exec && std::find(g.codes.begin(), g.codes.end(), code) != g.codes.end()) free_multi(g);
+}
+}  // namespace qc
+
+extern "C" size_t qcldpc_decode_multi_workspace(int n_codes, const qcldpc_code *const *codes,
+                                                const int *n_frames, const qcldpc_params *p) {
+    if (n_codes < 1 || n_codes > kMultiMaxCodes || !codes || !n_frames) return 0;
+    const int fmt = p ? p->msg_format : 0;
+    if (fmt < 0 || fmt > 2) return 0;
+    size_t total = 0;
+    for (int c = 0; c < n_codes; c++) {
+        if (!codes[c] || n_frames[c] < 0 || n_frames[c] > 65535) return 0;
+        total = align_up(total, 256) + layout_of(codes[c]->tab, n_frames[c], false, fmt).total;
+    }
+    return total;
+}
+
+extern "C" int qcldpc_decode_multi(int n_codes, const qcldpc_code *const *codes, const float *const *llr_dev,
+                                   const uint32_t *const *syn_dev, const int *n_frames, int max_iter,
+                                   const qcldpc_params *p_in, uint32_t *const *key_bits_dev,
+                                   int32_t *const *converged_dev, int32_t *const *iters_dev,
+                                   void *workspace_dev, size_t workspace_bytes, qcldpc_stream_t stream) {
+    using namespace qc;
+    if (n_codes < 1 || n_codes > kMultiMaxCodes)
+        return fail(QCLDPC_E_INVAL, "decode_multi: n_codes must be in [1, QCLDPC_MULTI_MAX_CODES]");
+    if (!codes || !llr_dev || !syn_dev || !n_frames || !key_bits_dev || !converged_dev || !iters_dev ||
+        !workspace_dev)
+        return fail(QCLDPC_E_INVAL, "decode_multi: NULL array");
+    if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode_multi: max_iter must be >= 0");
+    qcldpc_params p;
+    if (p_in) p = *p_in;
+    else qcldpc_params_init(&p);
+    if (!multi_params_ok(p))
+        return fail(QCLDPC_E_INVAL,
+                    "decode_multi: unsupported option (flooding only, no soft output, msg_format 0..2)");
+    if (!aligned(workspace_dev, 256)) return fail(QCLDPC_E_ALIGN, "decode_multi: workspace must be 256-byte aligned");
+    int dev = -1;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return cuda_fail(err, "decode_multi: cudaGetDevice");
+    std::vector<const qcldpc_code *> used;
+    std::vector<Work> works;
+    size_t off = 0;
+    for (int c = 0; c < n_codes; c++) {
+        qcldpc_code *code = const_cast<qcldpc_code *>(codes[c]);
+        const int F = n_frames[c];
+        if (!code) return fail(QCLDPC_E_INVAL, "decode_multi: NULL code");
+        if (F < 0 || F > 65535) return fail(QCLDPC_E_INVAL, "decode_multi: n_frames must be in [0, 65535]");
+        if (dev != code->device) return fail(QCLDPC_E_INVAL, "decode_multi: a code belongs to another device");
+        if (int st = upload_tables(code)) return st;
+        const Layout lo = layout_of(code->tab, F, false, p.msg_format);
+        off = align_up(off, 256);
+        char *base = static_cast<char *>(workspace_dev) + off;
+        off += lo.total;
+        if (F == 0) continue;
+        if (!llr_dev[c] || !syn_dev[c] || !key_bits_dev[c] || !converged_dev[c] || !iters_dev[c])
+            return fail(QCLDPC_E_INVAL, "decode_multi: NULL buffer");
+        if (!aligned(llr_dev[c], 16) || !aligned(syn_dev[c], 4) || !aligned(key_bits_dev[c], 4) ||
+            !aligned(converged_dev[c], 4) || !aligned(iters_dev[c], 4))
+            return fail(QCLDPC_E_ALIGN, "decode_multi: LLRs must be 16-byte aligned, other buffers 4-byte aligned");
+        used.push_back(code);
+        works.push_back(make_work(code, p, F, max_iter, llr_dev[c], syn_dev[c], key_bits_dev[c], converged_dev[c],
+                                  iters_dev[c], nullptr, base, lo));
+    }
+    if (workspace_bytes < off) return fail(QCLDPC_E_NOMEM, "decode_multi: workspace too small");
+    if (used.empty()) return QCLDPC_OK;
+    std::lock_guard<std::mutex> lock(g_mdec_mu);
+    MultiDecodeGraph *hit = nullptr, *victim = &g_mdec[0];
+    for (auto &g : g_mdec) {
+        if (g.exec && g.codes == used && g.works.size() == works.size() &&
+            std::memcmp(g.works.data(), works.data(), sizeof(Work) * works.size()) == 0)
+            hit = &g;
+        if (!g.exec || (victim->exec && g.stamp < victim->stamp)) victim = &g;
+    }
+    if (!hit) {
+        free_multi(*victim);
+        if (int st = build_multi_graph(*victim, used, works)) {
+            free_multi(*victim);
+            return st;
+        }
+        hit = victim;
+    }
+    hit->stamp = ++g_mdec_clock;
+    if ((err = cudaGraphLaunch(hit->exec, (cudaStream_t)stream)) != cudaSuccess)
+        return cuda_fail(err, "decode_multi: cudaGraphLaunch");
+    clear_error();
+    return QCLDPC_OK;
 }
 
 extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,

@@ -144,6 +144,8 @@ void clear_error();
 
 // Release decoder graph state of a code (decode.cu).
 void destroy_graph_cache(qcldpc_code *code);
+// Drop cached batched-decode graphs that decode this code (decode.cu).
+void purge_multi_graphs(const qcldpc_code *code);
 
 inline bool aligned(const void *p, size_t a) {
     return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0;

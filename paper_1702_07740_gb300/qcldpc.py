@@ -28,7 +28,8 @@ EXPORTED = [
     "qcldpc_syndrome", "qcldpc_bob_message_8d", "qcldpc_llr_8d",
     "qcldpc_bob_message", "qcldpc_llr",
     "qcldpc_params_init", "qcldpc_decode_workspace", "qcldpc_decode",
-    "qcldpc_decode_soft", "qcldpc_time_passes", "qcldpc_decode_noalloc", "qcldpc_autotune",
+    "qcldpc_decode_soft", "qcldpc_decode_multi_workspace", "qcldpc_decode_multi",
+    "qcldpc_time_passes", "qcldpc_decode_noalloc", "qcldpc_autotune",
     "qcldpc_autotune_shapes",
     "qcldpc_pool_workspace", "qcldpc_pool_create", "qcldpc_pool_destroy", "qcldpc_pool_state",
     "qcldpc_pool_load", "qcldpc_pool_step", "qcldpc_pools_step", "qcldpc_pool_collect",
@@ -104,6 +105,11 @@ def load(build_if_missing: bool = True):
         lib.qcldpc_decode.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
                                       vp, vp, vp, vp, sz, vp]
         lib.qcldpc_decode.restype = i32
+        lib.qcldpc_decode_multi_workspace.argtypes = [i32, vp, vp, ctypes.POINTER(qcldpc_params)]
+        lib.qcldpc_decode_multi_workspace.restype = sz
+        lib.qcldpc_decode_multi.argtypes = [i32, vp, vp, vp, vp, i32, ctypes.POINTER(qcldpc_params),
+                                            vp, vp, vp, vp, sz, vp]
+        lib.qcldpc_decode_multi.restype = i32
         lib.qcldpc_decode_soft.argtypes = [vp, vp, vp, i32, i32, ctypes.POINTER(qcldpc_params),
                                            vp, vp, vp, vp, vp, sz, vp]
         lib.qcldpc_decode_soft.restype = i32
@@ -295,6 +301,35 @@ def qcldpc_decode_soft(code: Code, llr_dev, syn_dev, n_frames: int, max_iter: in
     _check(st, "qcldpc_decode_soft")
 
 
+def _ptr_array(items, what):
+    arr = (ctypes.c_void_p * len(items))()
+    for i, t in enumerate(items):
+        arr[i] = _dev(t, None, what).value if t is not None else None
+    return arr
+
+
+def qcldpc_decode_multi_workspace(codes: list, n_frames: list, params: qcldpc_params | None = None) -> int:
+    hs = (ctypes.c_void_p * len(codes))(*[c.handle for c in codes])
+    nf = (ctypes.c_int * len(codes))(*[int(f) for f in n_frames])
+    p = ctypes.byref(params) if params is not None else None
+    return int(load().qcldpc_decode_multi_workspace(len(codes), hs, nf, p))
+
+
+def qcldpc_decode_multi(codes: list, llr_devs: list, syn_devs: list, n_frames: list, max_iter: int,
+                        params: qcldpc_params | None, key_bits_devs: list, converged_devs: list,
+                        iters_devs: list, workspace_dev, workspace_bytes: int, stream=None):
+    n = len(codes)
+    hs = (ctypes.c_void_p * n)(*[c.handle for c in codes])
+    nf = (ctypes.c_int * n)(*[int(f) for f in n_frames])
+    p = ctypes.byref(params) if params is not None else None
+    st = load().qcldpc_decode_multi(n, hs, _ptr_array(llr_devs, "llr_dev"), _ptr_array(syn_devs, "syn_dev"),
+                                    nf, int(max_iter), p, _ptr_array(key_bits_devs, "key_bits_dev"),
+                                    _ptr_array(converged_devs, "converged_dev"),
+                                    _ptr_array(iters_devs, "iters_dev"), _dev(workspace_dev, None, "workspace"),
+                                    int(workspace_bytes), _stream(stream))
+    _check(st, "qcldpc_decode_multi")
+
+
 def qcldpc_time_passes(code: Code, n_frames: int, workspace_dev, workspace_bytes: int,
                        reps: int, stream=None):
     """Mean (check-node ms, variable-node ms) of replayed decoder passes."""
@@ -359,6 +394,30 @@ def qcldpc_decode_noalloc(code: Code, llr_dev, syn_dev, n_frames: int, max_iter:
                                       _dev(converged_dev, 4, "converged_dev"),
                                       _dev(iters_dev, 4, "iters_dev"), _stream(stream))
     _check(st, "qcldpc_decode_noalloc")
+
+
+class MultiDecoder:
+    """Owner of the device buffers of a batched decode of several codes
+    (``qcldpc_decode_multi``): ``codes[c]`` decodes ``n_frames[c]`` frames;
+    ``keys[c]``, ``converged[c]`` and ``iters[c]`` hold its outputs."""
+
+    def __init__(self, codes: list, n_frames: list, params: qcldpc_params | None = None, device=None):
+        import torch
+        self.codes, self.n_frames = list(codes), [int(f) for f in n_frames]
+        self.params = params if params is not None else qcldpc_params_init()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.ws_bytes = qcldpc_decode_multi_workspace(self.codes, self.n_frames, self.params)
+        if self.ws_bytes == 0:
+            raise QcldpcError(-1, "qcldpc_decode_multi_workspace", "invalid arguments")
+        self.workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        self.keys = [torch.zeros(max(f, 1) * ((c.k + 31) // 32), dtype=torch.int32, device=dev)
+                     for c, f in zip(self.codes, self.n_frames)]
+        self.converged = [torch.zeros(max(f, 1), dtype=torch.int32, device=dev) for f in self.n_frames]
+        self.iters = [torch.zeros(max(f, 1), dtype=torch.int32, device=dev) for f in self.n_frames]
+
+    def decode(self, llr_devs: list, syn_devs: list, max_iter: int, stream=None):
+        qcldpc_decode_multi(self.codes, llr_devs, syn_devs, self.n_frames, max_iter, self.params, self.keys,
+                            self.converged, self.iters, self.workspace, self.ws_bytes, stream)
 
 
 class Decoder:

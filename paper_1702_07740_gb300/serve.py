@@ -1,19 +1,30 @@
-"""Continuous-batching request loop over the library's pools (one pool per code).
+"""Continuous-batching request loop over the library's pools.
 
-A ``Server`` owns one ``Pool`` per code and admits requests by device-memory
-footprint: the pools' workspaces are sized at start-up so that their sum fits
-the given budget, and a request waits until its code's pool has a free slot.
+A ``Server`` admits each request against one device-memory budget shared by
+all codes. Frame state lives in pool chunks: a chunk is a ``Pool`` of
+``chunk_slots`` slots of one code, and a code holds as many chunks as its
+requests need. A request is admitted when its code has a free slot, or when
+one more chunk of its code fits the budget; if the budget is full, chunks
+with no frame in them (of any code) are released first. So memory that one
+code no longer uses goes to another, and a request waits only while every
+byte of the budget holds running frames. Waiting requests are scanned in
+arrival order, and one that cannot be placed does not hold back later
+requests of codes that have room.
+
 Each ``tick``:
 
-1. loads waiting requests into free slots (one ``qcldpc_pool_load`` per frame,
-   straight from the request's own device buffers);
-2. steps every pool by ``passes`` iteration passes in one graph launch
-   (``qcldpc_pools_step``), so frames of all codes and all ages share the GPU;
-3. reads the slot states of all pools in one device-to-host copy and collects
-   each pool's stopped frames in one ``qcldpc_pool_collect``, which frees
-   their slots for the next tick.
+1. admits waiting requests (one ``qcldpc_pool_load`` per frame, straight from
+   the request's own device buffers, ordered after the writes that produced
+   them);
+2. steps every chunk that holds frames by ``passes`` iteration passes in one
+   graph launch (``qcldpc_pools_step``), so frames of all codes and all ages
+   share the GPU;
+3. reads the slot states of those chunks in one device-to-host copy and
+   collects each chunk's stopped frames in one ``qcldpc_pool_collect``, which
+   frees their slots for the next tick.
 
-Host-side scheduling only: all decoding runs in libqcldpc.
+Chunks that stay empty for ``idle_ticks`` ticks are released as well. Host-side
+scheduling only: all decoding runs in libqcldpc.
 """
 from __future__ import annotations
 
@@ -51,30 +62,96 @@ class Result:
         return self.t_done - self.t_arrival
 
 
+class _Chunk:
+    """One pool of a code with its slot bookkeeping and output buffers."""
+
+    def __init__(self, name, code, n_slots, max_iter, params, stream):
+        self.name, self.n_slots = name, n_slots
+        self.pool = q.Pool(code, n_slots, max_iter, params, stream)
+        self.bytes = self.pool.ws_bytes
+        self.slot_ids = torch.arange(n_slots, dtype=torch.int32, device="cuda")
+        self.free = collections.deque(range(n_slots))
+        self.busy = {}           # slot -> Request
+        self.idle = 0            # consecutive ticks without a frame
+        wk = (code.k + 31) // 32
+        self.out = (torch.empty((n_slots, wk), dtype=torch.int32, device="cuda"),
+                    torch.empty(n_slots, dtype=torch.int32, device="cuda"),
+                    torch.empty(n_slots, dtype=torch.int32, device="cuda"))
+
+
 class Server:
-    def __init__(self, codes: dict, slots: dict, max_iter: int, params=None,
-                 hbm_budget_bytes: int | None = None, stream=None):
+    """codes: name -> Code. hbm_budget_bytes caps the sum of the chunks' pool
+    workspaces (None: no cap). chunk_slots: slots per chunk, the unit in which
+    a code's frame state grows and shrinks. slots (optional): name -> slots
+    to allocate up front (rounded up to whole chunks)."""
+
+    def __init__(self, codes: dict, max_iter: int, params=None, hbm_budget_bytes: int | None = None,
+                 chunk_slots: int = 16, slots: dict | None = None, idle_ticks: int = 64, stream=None):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = params if params is not None else q.qcldpc_params_init()
-        need = {name: q.qcldpc_pool_workspace(codes[name], slots[name], self.params) for name in codes}
-        if hbm_budget_bytes is not None and sum(need.values()) > hbm_budget_bytes:
-            raise ValueError(f"pools need {sum(need.values())} bytes, budget {hbm_budget_bytes}")
-        self.codes = codes
-        self.pools = {name: q.Pool(codes[name], slots[name], max_iter, self.params, self.stream)
-                      for name in codes}
-        self.footprint = sum(need.values())
-        self.slot_ids = {name: torch.arange(slots[name], dtype=torch.int32, device="cuda")
-                         for name in codes}
-        self.free = {name: collections.deque(range(slots[name])) for name in codes}
-        self.busy = {name: {} for name in codes}   # slot -> Request
-        self.queue = {name: collections.deque() for name in codes}
-        self.out = {}
-        for name, code in codes.items():
-            wk = (code.k + 31) // 32
-            s = slots[name]
-            self.out[name] = (torch.empty((s, wk), dtype=torch.int32, device="cuda"),
-                              torch.empty(s, dtype=torch.int32, device="cuda"),
-                              torch.empty(s, dtype=torch.int32, device="cuda"))
+        self.codes, self.max_iter = codes, max_iter
+        self.budget = hbm_budget_bytes
+        self.chunk_slots, self.idle_ticks = chunk_slots, idle_ticks
+        self.chunk_bytes = {name: q.qcldpc_pool_workspace(codes[name], chunk_slots, self.params)
+                            for name in codes}
+        if self.budget is not None and min(self.chunk_bytes.values()) > self.budget:
+            raise ValueError(f"no chunk fits the budget of {self.budget} bytes")
+        self.chunks = {name: [] for name in codes}
+        self.used = 0
+        self.peak_used = 0
+        self.queue = collections.deque()
+        for name, s in (slots or {}).items():
+            for _ in range(-(-s // chunk_slots)):
+                if not self._grow(name):
+                    raise ValueError(f"initial slots of {name} exceed the budget")
+
+    # ------------------------------------------------------------ memory
+
+    @property
+    def footprint(self) -> int:
+        """Bytes of device memory the chunks hold now."""
+        return self.used
+
+    def _grow(self, name) -> _Chunk | None:
+        need = self.chunk_bytes[name]
+        if self.budget is not None and self.used + need > self.budget:
+            return None
+        with torch.cuda.stream(self.stream):
+            ch = _Chunk(name, self.codes[name], self.chunk_slots, self.max_iter, self.params,
+                        self.stream)
+        self.chunks[name].append(ch)
+        self.used += ch.bytes
+        self.peak_used = max(self.peak_used, self.used)
+        return ch
+
+    def _release(self, ch: _Chunk):
+        # the server's stream is idle here: every tick ends with a blocking
+        # read of its results
+        self.chunks[ch.name].remove(ch)
+        self.used -= ch.bytes
+        del ch.pool
+
+    def _reclaim(self, need: int) -> bool:
+        """Release empty chunks, longest idle first, until `need` more bytes
+        fit the budget."""
+        empty = sorted((ch for cs in self.chunks.values() for ch in cs if not ch.busy),
+                       key=lambda ch: -ch.idle)
+        for ch in empty:
+            if self.used + need <= self.budget:
+                break
+            self._release(ch)
+        return self.used + need <= self.budget
+
+    def _place(self, name):
+        for ch in self.chunks[name]:
+            if ch.free:
+                return ch
+        ch = self._grow(name)
+        if ch is None and self._reclaim(self.chunk_bytes[name]):
+            ch = self._grow(name)
+        return ch
+
+    # ------------------------------------------------------------ requests
 
     def submit(self, req: Request):
         """Queue a request. Its buffers may still be being written on the
@@ -82,53 +159,68 @@ class Server:
         server's load of them after those writes."""
         req.ready = torch.cuda.Event()
         req.ready.record(torch.cuda.current_stream())
-        self.queue[req.code].append(req)
+        self.queue.append(req)
 
     def pending(self) -> int:
-        return sum(len(v) for v in self.queue.values()) + sum(len(v) for v in self.busy.values())
+        return len(self.queue) + sum(len(ch.busy) for cs in self.chunks.values() for ch in cs)
+
+    def slots(self) -> dict:
+        """Slots each code holds now."""
+        return {name: sum(ch.n_slots for ch in cs) for name, cs in self.chunks.items()}
+
+    def _admit(self):
+        waiting = collections.deque()
+        full = set()  # codes that found no room this tick
+        while self.queue:
+            req = self.queue.popleft()
+            ch = None if req.code in full else self._place(req.code)
+            if ch is None:
+                full.add(req.code)
+                waiting.append(req)
+                continue
+            s = ch.free.popleft()
+            if req.ready is not None:
+                self.stream.wait_event(req.ready)
+            q.qcldpc_pool_load(ch.pool, 1, ch.slot_ids[s:s + 1], req.llr, req.syn, self.stream)
+            ch.busy[s] = req
+        self.queue = waiting
 
     def tick(self, passes: int = 4) -> list:
-        for name, pool in self.pools.items():
-            ids = self.slot_ids[name]
-            while self.queue[name] and self.free[name]:
-                req = self.queue[name].popleft()
-                s = self.free[name].popleft()
-                if req.ready is not None:
-                    self.stream.wait_event(req.ready)
-                q.qcldpc_pool_load(pool, 1, ids[s:s + 1], req.llr, req.syn, self.stream)
-                self.busy[name][s] = req
-        names = [name for name in self.pools if self.busy[name]]
-        if not names:
+        self._admit()
+        live = [ch for cs in self.chunks.values() for ch in cs if ch.busy]
+        for cs in self.chunks.values():
+            for ch in list(cs):
+                ch.idle = 0 if ch.busy else ch.idle + 1
+                if ch.idle > self.idle_ticks:
+                    self._release(ch)
+        if not live:
             return []
-        q.qcldpc_pools_step([self.pools[name] for name in names], passes, self.stream)
-        # one device->host read of every busy pool's slot states (waits for the passes)
+        q.qcldpc_pools_step([ch.pool for ch in live], passes, self.stream)
+        # one device->host read of every stepped chunk's slot states (waits for the passes)
         with torch.cuda.stream(self.stream):
-            states = torch.cat([self.pools[name].state for name in names]).cpu().tolist()
+            states = torch.cat([ch.pool.state for ch in live]).cpu().tolist()
         now = time.perf_counter()
         done, collected, off = [], [], 0
-        for name in names:
-            pool = self.pools[name]
-            st = states[off: off + pool.n_slots]
-            off += pool.n_slots
-            stopped = [s for s in self.busy[name] if st[s] == 2]
+        for ch in live:
+            st = states[off: off + ch.n_slots]
+            off += ch.n_slots
+            stopped = [s for s in ch.busy if st[s] == 2]
             if not stopped:
                 continue
-            keys, conv, iters = self.out[name]
+            keys, conv, iters = ch.out
             with torch.cuda.stream(self.stream):
-                sel = torch.tensor(stopped, dtype=torch.int32).to(self.slot_ids[name].device)
+                sel = torch.tensor(stopped, dtype=torch.int32).to(ch.slot_ids.device)
             n = len(stopped)
-            q.qcldpc_pool_collect(pool, n, sel, keys[:n], conv[:n], iters[:n], self.stream)
-            collected.append((name, stopped))
+            q.qcldpc_pool_collect(ch.pool, n, sel, keys[:n], conv[:n], iters[:n], self.stream)
+            collected.append((ch, stopped))
         if collected:
             with torch.cuda.stream(self.stream):
-                host = {name: tuple(t[:len(stopped)].cpu() for t in self.out[name])
-                        for name, stopped in collected}
-            for name, stopped in collected:
-                k_h, c_h, i_h = host[name]
+                host = [tuple(t[:len(stopped)].cpu() for t in ch.out) for ch, stopped in collected]
+            for (ch, stopped), (k_h, c_h, i_h) in zip(collected, host):
                 for j, s in enumerate(stopped):
-                    req = self.busy[name].pop(s)
-                    self.free[name].append(s)
-                    done.append(Result(req.tag, name, k_h[j].clone(), int(c_h[j]), int(i_h[j]),
+                    req = ch.busy.pop(s)
+                    ch.free.append(s)
+                    done.append(Result(req.tag, ch.name, k_h[j].clone(), int(c_h[j]), int(i_h[j]),
                                        req.t_arrival, now))
         return done
 

@@ -1,0 +1,118 @@
+"""Batched decoding of several codes in one graph launch (qcldpc_decode_multi)
+against one qcldpc_decode call per code and against the FP64 oracle.
+
+Every frame keeps its own stop test inside the shared device loop, so the
+key bits, flags and stop iterations must equal the one-code decodes bit for
+bit, for every storage format; against the oracle the flags and iterations
+are equal on every frame and the key bits on every converged frame
+(the bar of test_gpu_parity)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from frames import make_frames
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1702_07740_gb300 import qcldpc as q  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device visible")
+    q.load()
+
+
+def _inputs(fr):
+    F, n = fr.F, fr.code.n
+    llr = torch.empty(F * n, dtype=torch.float32, device="cuda")
+    q.qcldpc_llr_8d(torch.from_numpy(fr.x32.reshape(-1)).cuda(),
+                    torch.from_numpy(fr.m32.reshape(-1)).cuda(), F * n, fr.snr, llr)
+    syn = torch.from_numpy(synth.pack_bits(fr.syn).view(np.int32).reshape(-1)).cuda()
+    return llr, syn
+
+
+def _unpack(keys, F, k):
+    wk = (k + 31) // 32
+    return synth.unpack_bits(keys.cpu().numpy().view(np.uint32)[: F * wk].reshape(F, wk), k)
+
+
+# (code maker, Z, SNR, frames): rates 0.02, 0.05 and 0.10, ragged frame counts
+MIX = [(synth.rate002_code, 64, 0.08, 5), (synth.rate005_code, 100, 0.2, 3),
+       (synth.rate010_code, 160, 0.35, 7)]
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_multi_equals_one_decode_per_code_and_the_oracle(fmt):
+    max_iter = 60
+    params = q.qcldpc_params_init(msg_format=fmt)
+    frs, codes, ins = [], [], []
+    for i, (mk, Z, snr, F) in enumerate(MIX):
+        fr = make_frames(mk(Z), snr, F, seed0=9000 + 100 * i)
+        frs.append(fr)
+        codes.append(q.create_code_from(fr.code_dict))
+        ins.append(_inputs(fr))
+    md = q.MultiDecoder(codes, [fr.F for fr in frs], params)
+    md.decode([x[0] for x in ins], [x[1] for x in ins], max_iter)
+    torch.cuda.synchronize()
+    n_conv = 0
+    for c, fr in enumerate(frs):
+        one = q.Decoder(codes[c], fr.F, params)
+        one.decode(ins[c][0], ins[c][1], max_iter)
+        torch.cuda.synchronize()
+        F = fr.F
+        assert torch.equal(md.keys[c][: one.keys.numel()], one.keys), c
+        assert torch.equal(md.converged[c][:F], one.converged), c
+        assert torch.equal(md.iters[c][:F], one.iters), c
+        if fmt != 0:
+            continue
+        keys = _unpack(md.keys[c], F, fr.code.k)
+        conv, its = md.converged[c][:F].cpu().numpy(), md.iters[c][:F].cpu().numpy()
+        for f in range(F):
+            _, chat, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], max_iter)
+            assert (its[f], conv[f]) == (it, int(cv)), (c, f)
+            if cv:
+                n_conv += 1
+                np.testing.assert_array_equal(keys[f], chat[: fr.code.k], f"code {c} frame {f}")
+    if fmt == 0:
+        assert 0 < n_conv < sum(fr.F for fr in frs)
+
+
+def test_multi_with_a_repeated_code_and_an_empty_entry():
+    """The same code twice (two frame groups with their own workspace parts)
+    and a code with no frame."""
+    max_iter = 40
+    d = synth.rate002_code(64)
+    fa = make_frames(d, 0.08, 3, seed0=9500)
+    fb = make_frames(d, 0.08, 2, seed0=9600)
+    code = q.create_code_from(d)
+    other = q.create_code_from(synth.rate010_code(160))
+    ia, ib = _inputs(fa), _inputs(fb)
+    md = q.MultiDecoder([code, other, code], [3, 0, 2])
+    md.decode([ia[0], None, ib[0]], [ia[1], None, ib[1]], max_iter)
+    torch.cuda.synchronize()
+    for slot, fr, inp in ((0, fa, ia), (2, fb, ib)):
+        one = q.Decoder(code, fr.F)
+        one.decode(inp[0], inp[1], max_iter)
+        torch.cuda.synchronize()
+        assert torch.equal(md.keys[slot][: one.keys.numel()], one.keys)
+        assert torch.equal(md.iters[slot][: fr.F], one.iters)
+        assert torch.equal(md.converged[slot][: fr.F], one.converged)
+
+
+def test_multi_rejects_bad_arguments():
+    code = q.create_code_from(synth.rate002_code(64))
+    assert q.qcldpc_decode_multi_workspace([code], [1], q.qcldpc_params_init(msg_format=5)) == 0
+    assert q.qcldpc_decode_multi_workspace([code] * 17, [1] * 17) == 0
+    md = q.MultiDecoder([code], [1])
+    x = torch.zeros(code.n, device="cuda")
+    s = torch.zeros((code.m + 31) // 32, dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QcldpcError, match="INVAL"):
+        q.qcldpc_decode_multi([code], [x], [s], [1], 10, q.qcldpc_params_init(schedule=1), md.keys,
+                              md.converged, md.iters, md.workspace, md.ws_bytes)
+    with pytest.raises(q.QcldpcError, match="NOMEM"):
+        q.qcldpc_decode_multi([code], [x], [s], [1], 10, None, md.keys, md.converged, md.iters,
+                              md.workspace, 256)

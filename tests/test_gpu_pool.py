@@ -22,14 +22,15 @@ def _gpu():
     q.load()
 
 
-def _frames(code_dict, snr, F, seed0):
+def _frames(code_dict, snr, F, seed0, with_oracle_inputs=False):
     fr = make_frames(code_dict, snr, F, seed0=seed0)
     n = fr.code.n
     llr = torch.empty(F * n, dtype=torch.float32, device="cuda")
     q.qcldpc_llr_8d(torch.from_numpy(fr.x32.reshape(-1)).cuda(),
                     torch.from_numpy(fr.m32.reshape(-1)).cuda(), F * n, snr, llr)
     syn = torch.from_numpy(synth.pack_bits(fr.syn).view(np.int32)).cuda()
-    return [(llr[f * n:(f + 1) * n], syn[f]) for f in range(F)]
+    out = [(llr[f * n:(f + 1) * n], syn[f]) for f in range(F)]
+    return (out, fr) if with_oracle_inputs else out
 
 
 def _alone(code, llr, syn, max_iter, params=None):
@@ -45,16 +46,32 @@ MIX = {"r002": (synth.rate002_code, 64, 0.08), "r005": (synth.rate005_code, 100,
 
 @pytest.mark.parametrize("schedule", [0, 1])
 def test_server_results_equal_alone_decoding_for_a_mix_of_codes(schedule):
-    """Flooding, and layered with one row group per base row."""
+    """Flooding, and layered with one row group per base row. Every served
+    frame is also checked against the FP64 oracle (the flooding or the
+    layered routine): the same stop iteration and flag on every frame, and
+    the oracle's key bits on every frame that converged."""
+    import oracle
     max_iter = 60
     params = q.qcldpc_params_init(schedule=schedule)
-    codes, frames = {}, []
+    codes, frames, refs = {}, [], {}
     for i, (name, (mk, Z, snr)) in enumerate(MIX.items()):
         d = mk(Z)
         codes[name] = q.create_code_from(d)
-        for j, (llr, syn) in enumerate(_frames(d, snr, 7, 7000 + 100 * i)):
+        pairs, fr = _frames(d, snr, 7, 7000 + 100 * i, with_oracle_inputs=True)
+        for j, (llr, syn) in enumerate(pairs):
             frames.append((name, j, llr, syn))
-    srv = serve.Server(codes, {"r002": 3, "r005": 2, "r010": 4}, max_iter, params)
+            if schedule == 0:
+                refs[(name, j)] = oracle.decode(fr.code, fr.q64[j], fr.syn[j], max_iter)
+            else:
+                layers = oracle.row_layers(fr.code, d["mb"])
+                refs[(name, j)] = oracle.decode_layered(fr.code, fr.q64[j], fr.syn[j], max_iter, layers)
+            refs[(name, j)] = refs[(name, j)] + (fr.code.k,)
+    # a budget of four two-slot chunks: requests wait for room, and empty
+    # chunks of one code are released for another
+    chunk = 2
+    budget = 4 * max(q.qcldpc_pool_workspace(c, chunk, params) for c in codes.values())
+    srv = serve.Server(codes, max_iter, params, hbm_budget_bytes=budget, chunk_slots=chunk,
+                       idle_ticks=2)
     # arrivals spread over ticks: two frames per tick, interleaved codes
     order = sorted(frames, key=lambda t: (t[1], t[0]))
     results = {}
@@ -66,14 +83,55 @@ def test_server_results_equal_alone_decoding_for_a_mix_of_codes(schedule):
         for r in srv.tick(passes=3):
             results[r.tag] = r
     assert len(results) == len(frames)
+    assert srv.peak_used <= budget and srv.footprint <= budget
     n_conv = 0
     for name, j, llr, syn in frames:
         keys, conv, iters = _alone(codes[name], llr, syn, max_iter, params)
         r = results[(name, j)]
         assert (r.converged, r.iters) == (conv, iters), (name, j)
         assert torch.equal(r.keys, keys.view(-1)), (name, j)
+        _, chat, it_ref, cv_ref, k = refs[(name, j)]
+        assert (r.converged, r.iters) == (int(cv_ref), it_ref), ("oracle", name, j)
+        if cv_ref:
+            got = synth.unpack_bits(r.keys.numpy().view(np.uint32)[None, :], k)[0]
+            np.testing.assert_array_equal(got, chat[:k], f"oracle keys {name} {j}")
         n_conv += conv
     assert 0 < n_conv and (schedule == 1 or n_conv < len(frames))
+
+
+def test_server_moves_memory_between_codes():
+    """With a budget of one chunk, a request of another code is admitted by
+    releasing the empty chunk of the first code (per-request admission
+    against one shared budget), and a request waits while the budget is
+    held by running frames."""
+    max_iter = 40
+    params = q.qcldpc_params_init()
+    da, db = synth.rate002_code(64), synth.rate010_code(160)
+    codes = {"a": q.create_code_from(da), "b": q.create_code_from(db)}
+    fa = _frames(da, 0.08, 2, 8100)
+    fb = _frames(db, 0.35, 2, 8200)
+    budget = max(q.qcldpc_pool_workspace(c, 2, params) for c in codes.values())
+    srv = serve.Server(codes, max_iter, params, hbm_budget_bytes=budget, chunk_slots=2,
+                       idle_ticks=1000)
+    for j, (llr, syn) in enumerate(fa):
+        srv.submit(serve.Request("a", llr, syn, tag=("a", j)))
+    srv.submit(serve.Request("b", fb[0][0], fb[0][1], tag=("b", 0)))
+    out = srv.tick(passes=1)
+    # code a took the only chunk; the b request waits
+    assert srv.slots() == {"a": 2, "b": 0} and len(srv.queue) == 1
+    res = {r.tag: r for r in out}
+    while len(res) < 2:
+        res.update({r.tag: r for r in srv.tick(passes=4)})
+    srv.submit(serve.Request("b", fb[1][0], fb[1][1], tag=("b", 1)))
+    res.update({r.tag: r for r in srv.drain(passes=4)})
+    assert srv.slots() == {"a": 0, "b": 2}
+    assert srv.peak_used <= budget
+    for name, fr in (("a", fa), ("b", fb)):
+        for j, (llr, syn) in enumerate(fr):
+            keys, conv, iters = _alone(codes[name], llr, syn, max_iter, params)
+            r = res[(name, j)]
+            assert (r.converged, r.iters) == (conv, iters)
+            assert torch.equal(r.keys, keys.view(-1))
 
 
 def test_pool_slots_are_reused_and_states_track_frames():
