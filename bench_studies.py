@@ -433,20 +433,21 @@ def study_serve(args):
     names = [name for name, _, _, _ in MIX]
     params = q.qcldpc_params_init(msg_format=FMT["fp16"])
     slots = {name: 32 for name in names}
-    chunk = 16
+    chunk = 32
     passes = 4
     budget = 64 << 30
     bits = {c: codes[c].n for c in names}
     # capacity: a saturated burst (every request present at t = 0)
     rng = np.random.default_rng(12345)
     burst = [(0.0, names[j % len(names)], int(rng.integers(0, n_bank)))
-             for j in range(len(names) * 64)]
+             for j in range(len(names) * 256)]
     srv = serve.Server(codes, args.max_iter, params, hbm_budget_bytes=budget, chunk_slots=chunk,
                        slots=slots)
     serve_once(srv, codes, bank, burst[:30], passes)  # warm-up: graphs instantiated
     lat, err, sec, _ = serve_once(srv, codes, bank, burst, passes)
     footprint = srv.footprint
     cap_fps = len(burst) / sec
+    srv.warm(passes)  # the chunks the burst grew get their step graphs before the sweep
     per_frame = PerFrame(codes)
     fifo_once(per_frame, bank, args.max_iter, burst[:12])  # warm-up of the per-frame decoder
     emit({"study": "serve", "phase": "capacity", "frames": len(burst), "seconds": sec,

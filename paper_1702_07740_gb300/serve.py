@@ -1,9 +1,11 @@
 """Continuous-batching request loop over the library's pools.
 
 A ``Server`` admits each request against one device-memory budget shared by
-all codes. Frame state lives in pool chunks: a chunk is a ``Pool`` of
-``chunk_slots`` slots of one code, and a code holds as many chunks as its
-requests need. A request is admitted when its code has a free slot, or when
+all codes. Frame state lives in pool chunks: a chunk is a ``Pool`` of slots of
+one code, and a code holds as many chunks as its requests need. A code's
+first chunk has ``chunk_slots`` slots and each further one twice as many as
+the previous (at most ``max_chunk_slots``), so a busy code holds a few large
+chunks rather than many small ones. A request is admitted when its code has a free slot, or when
 one more chunk of its code fits the budget; if the budget is full, chunks
 with no frame in them (of any code) are released first. So memory that one
 code no longer uses goes to another, and a request waits only while every
@@ -16,15 +18,19 @@ Each ``tick``:
 1. admits waiting requests (one ``qcldpc_pool_load`` per frame, straight from
    the request's own device buffers, ordered after the writes that produced
    them);
-2. steps every chunk that holds frames by ``passes`` iteration passes in one
-   graph launch (``qcldpc_pools_step``), so frames of all codes and all ages
-   share the GPU;
+2. steps every chunk that holds frames by ``passes`` iteration passes, each
+   chunk with its own cached step graph (``qcldpc_pool_step``) on one of a
+   few side streams, so frames of all codes and all ages share the GPU and no
+   graph is rebuilt when the set of busy chunks changes;
 3. reads the slot states of those chunks in one device-to-host copy and
    collects each chunk's stopped frames in one ``qcldpc_pool_collect``, which
    frees their slots for the next tick.
 
-Chunks that stay empty for ``idle_ticks`` ticks are released as well. Host-side
-scheduling only: all decoding runs in libqcldpc.
+Chunks that stay empty for ``idle_seconds`` are released as well (and
+created again when their code needs them, which costs a workspace
+allocation and a graph instantiation; ``warm`` instantiates the step graphs
+of the chunks a server holds). Host-side scheduling only: all
+decoding runs in libqcldpc.
 """
 from __future__ import annotations
 
@@ -72,7 +78,7 @@ class _Chunk:
         self.slot_ids = torch.arange(n_slots, dtype=torch.int32, device="cuda")
         self.free = collections.deque(range(n_slots))
         self.busy = {}           # slot -> Request
-        self.idle = 0            # consecutive ticks without a frame
+        self.idle_since = time.perf_counter()  # when the chunk last became empty
         wk = (code.k + 31) // 32
         self.out = (torch.empty((n_slots, wk), dtype=torch.int32, device="cuda"),
                     torch.empty(n_slots, dtype=torch.int32, device="cuda"),
@@ -81,17 +87,20 @@ class _Chunk:
 
 class Server:
     """codes: name -> Code. hbm_budget_bytes caps the sum of the chunks' pool
-    workspaces (None: no cap). chunk_slots: slots per chunk, the unit in which
-    a code's frame state grows and shrinks. slots (optional): name -> slots
-    to allocate up front (rounded up to whole chunks)."""
+    workspaces (None: no cap). chunk_slots: slots of a code's first chunk,
+    the smallest unit in which its frame state grows and shrinks; later
+    chunks double up to max_chunk_slots. slots (optional): name -> slots to
+    allocate up front."""
 
     def __init__(self, codes: dict, max_iter: int, params=None, hbm_budget_bytes: int | None = None,
-                 chunk_slots: int = 16, slots: dict | None = None, idle_ticks: int = 64, stream=None):
+                 chunk_slots: int = 16, slots: dict | None = None, idle_seconds: float = 30.0,
+                 stream=None, n_streams: int = 8, max_chunk_slots: int = 512):
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.side = [torch.cuda.Stream() for _ in range(n_streams)]
         self.params = params if params is not None else q.qcldpc_params_init()
         self.codes, self.max_iter = codes, max_iter
         self.budget = hbm_budget_bytes
-        self.chunk_slots, self.idle_ticks = chunk_slots, idle_ticks
+        self.chunk_slots, self.max_chunk_slots, self.idle_seconds = chunk_slots, max_chunk_slots, idle_seconds
         self.chunk_bytes = {name: q.qcldpc_pool_workspace(codes[name], chunk_slots, self.params)
                             for name in codes}
         if self.budget is not None and min(self.chunk_bytes.values()) > self.budget:
@@ -101,7 +110,7 @@ class Server:
         self.peak_used = 0
         self.queue = collections.deque()
         for name, s in (slots or {}).items():
-            for _ in range(-(-s // chunk_slots)):
+            while sum(ch.n_slots for ch in self.chunks[name]) < s:
                 if not self._grow(name):
                     raise ValueError(f"initial slots of {name} exceed the budget")
 
@@ -112,13 +121,16 @@ class Server:
         """Bytes of device memory the chunks hold now."""
         return self.used
 
-    def _grow(self, name) -> _Chunk | None:
-        need = self.chunk_bytes[name]
+    def _next_slots(self, name) -> int:
+        return min(self.max_chunk_slots, self.chunk_slots << len(self.chunks[name]))
+
+    def _grow(self, name, n_slots: int | None = None) -> _Chunk | None:
+        n_slots = n_slots or self._next_slots(name)
+        need = q.qcldpc_pool_workspace(self.codes[name], n_slots, self.params)
         if self.budget is not None and self.used + need > self.budget:
             return None
         with torch.cuda.stream(self.stream):
-            ch = _Chunk(name, self.codes[name], self.chunk_slots, self.max_iter, self.params,
-                        self.stream)
+            ch = _Chunk(name, self.codes[name], n_slots, self.max_iter, self.params, self.stream)
         self.chunks[name].append(ch)
         self.used += ch.bytes
         self.peak_used = max(self.peak_used, self.used)
@@ -135,7 +147,7 @@ class Server:
         """Release empty chunks, longest idle first, until `need` more bytes
         fit the budget."""
         empty = sorted((ch for cs in self.chunks.values() for ch in cs if not ch.busy),
-                       key=lambda ch: -ch.idle)
+                       key=lambda ch: ch.idle_since)
         for ch in empty:
             if self.used + need <= self.budget:
                 break
@@ -146,9 +158,11 @@ class Server:
         for ch in self.chunks[name]:
             if ch.free:
                 return ch
-        ch = self._grow(name)
+        # the next (doubled) chunk if it fits, else the smallest one, after
+        # releasing empty chunks if the budget needs it
+        ch = self._grow(name) or self._grow(name, self.chunk_slots)
         if ch is None and self._reclaim(self.chunk_bytes[name]):
-            ch = self._grow(name)
+            ch = self._grow(name, self.chunk_slots)
         return ch
 
     # ------------------------------------------------------------ requests
@@ -188,14 +202,26 @@ class Server:
     def tick(self, passes: int = 4) -> list:
         self._admit()
         live = [ch for cs in self.chunks.values() for ch in cs if ch.busy]
+        now = time.perf_counter()
         for cs in self.chunks.values():
             for ch in list(cs):
-                ch.idle = 0 if ch.busy else ch.idle + 1
-                if ch.idle > self.idle_ticks:
+                if not ch.busy and now - ch.idle_since >= self.idle_seconds:
                     self._release(ch)
         if not live:
             return []
-        q.qcldpc_pools_step([ch.pool for ch in live], passes, self.stream)
+        # fork: chunk i steps on side stream i mod n after this tick's loads,
+        # with its own cached graph; join before the states are read
+        start = torch.cuda.Event()
+        start.record(self.stream)
+        used = self.side[: min(len(self.side), len(live))]
+        for st in used:
+            st.wait_event(start)
+        for i, ch in enumerate(live):
+            q.qcldpc_pool_step(ch.pool, passes, used[i % len(used)])
+        for st in used:
+            ev = torch.cuda.Event()
+            ev.record(st)
+            self.stream.wait_event(ev)
         # one device->host read of every stepped chunk's slot states (waits for the passes)
         with torch.cuda.stream(self.stream):
             states = torch.cat([ch.pool.state for ch in live]).cpu().tolist()
@@ -220,9 +246,19 @@ class Server:
                 for j, s in enumerate(stopped):
                     req = ch.busy.pop(s)
                     ch.free.append(s)
+                    if not ch.busy:
+                        ch.idle_since = now
                     done.append(Result(req.tag, ch.name, k_h[j].clone(), int(c_h[j]), int(i_h[j]),
                                        req.t_arrival, now))
         return done
+
+    def warm(self, passes: int = 4):
+        """Instantiate the step graph of every chunk for `passes` (a step of
+        an empty chunk exits at once)."""
+        for cs in self.chunks.values():
+            for ch in cs:
+                q.qcldpc_pool_step(ch.pool, passes, self.stream)
+        self.stream.synchronize()
 
     def drain(self, passes: int = 4) -> list:
         out = []

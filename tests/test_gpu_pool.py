@@ -71,7 +71,7 @@ def test_server_results_equal_alone_decoding_for_a_mix_of_codes(schedule):
     chunk = 2
     budget = 4 * max(q.qcldpc_pool_workspace(c, chunk, params) for c in codes.values())
     srv = serve.Server(codes, max_iter, params, hbm_budget_bytes=budget, chunk_slots=chunk,
-                       idle_ticks=2)
+                       idle_seconds=0.0, max_chunk_slots=chunk)
     # arrivals spread over ticks: two frames per tick, interleaved codes
     order = sorted(frames, key=lambda t: (t[1], t[0]))
     results = {}
@@ -112,7 +112,7 @@ def test_server_moves_memory_between_codes():
     fb = _frames(db, 0.35, 2, 8200)
     budget = max(q.qcldpc_pool_workspace(c, 2, params) for c in codes.values())
     srv = serve.Server(codes, max_iter, params, hbm_budget_bytes=budget, chunk_slots=2,
-                       idle_ticks=1000)
+                       idle_seconds=1e9, max_chunk_slots=2)
     for j, (llr, syn) in enumerate(fa):
         srv.submit(serve.Request("a", llr, syn, tag=("a", j)))
     srv.submit(serve.Request("b", fb[0][0], fb[0][1], tag=("b", 0)))
@@ -132,6 +132,26 @@ def test_server_moves_memory_between_codes():
             r = res[(name, j)]
             assert (r.converged, r.iters) == (conv, iters)
             assert torch.equal(r.keys, keys.view(-1))
+
+
+def test_server_grows_a_busy_code_in_doubling_chunks():
+    """A code whose requests outnumber its slots grows by chunks of 2, 4 and
+    8 slots (doubling), and every frame decodes as it would alone."""
+    max_iter = 30
+    params = q.qcldpc_params_init()
+    d = synth.rate002_code(64)
+    code = q.create_code_from(d)
+    frames = _frames(d, 0.08, 14, 8300)
+    srv = serve.Server({"a": code}, max_iter, params, chunk_slots=2, max_chunk_slots=8)
+    for j, (llr, syn) in enumerate(frames):
+        srv.submit(serve.Request("a", llr, syn, tag=j))
+    res = {r.tag: r for r in srv.tick(passes=1)}
+    assert sorted(ch.n_slots for ch in srv.chunks["a"]) == [2, 4, 8]
+    res.update({r.tag: r for r in srv.drain(passes=4)})
+    for j, (llr, syn) in enumerate(frames):
+        keys, conv, iters = _alone(code, llr, syn, max_iter, params)
+        assert (res[j].converged, res[j].iters) == (conv, iters)
+        assert torch.equal(res[j].keys, keys.view(-1))
 
 
 def test_pool_slots_are_reused_and_states_track_frames():
