@@ -583,6 +583,11 @@ def run_ours(args, world, rank, local):
         "info_mbps": value * (k / n) * (1 - fer), "mean_iters": mean_iters,
         "step_ms_p50": float(np.percentile(step_ms, 50)),
         "step_ms_p99": float(np.percentile(step_ms, 99)),
+        # a frame's latency: device time from the start of its step's LLR map
+        # to the end of its decode (every frame of a step completes with it)
+        "frame_latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                             "p99": float(np.percentile(step_ms, 99)),
+                             "frames_per_step": F},
         "iteration_us_per_frame": iter_ms * 1e3 / F,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,

@@ -369,9 +369,11 @@ int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev, const uint32_
  * Launch-shape autotuner; the paper has no counterpart. On the state a
  * previous flooding qcldpc_decode / qcldpc_decode_soft call with the same
  * code, n_frames and workspace left behind, replays the check-node pass with
- * blocks of 32, 64, ..., 256 threads, and the variable-node pass with (nodes
- * per thread, vn_split) = (1,1), (2,1), (3,1), (1,2), (2,2), (3,2), each
- * `reps` times after one warm-up launch (CUDA events on `stream`).
+ * blocks of 32, 64, ..., 256 threads, and the separate variable-node pass
+ * (the one vn_pass = 1 selects) with (nodes per thread, vn_split) = (1,1),
+ * (2,1), (3,1), (1,2), (2,2), (3,2), each `reps` times after one warm-up
+ * launch (CUDA events on `stream`). The accumulated-posterior pass of
+ * vn_pass = 0 has one shape and is not tuned.
  *   p        options the shapes are tuned for (NULL = defaults)
  *   best     out: *p with cn_threads, vn_nodes and vn_split set to the
  *            fastest candidates
@@ -388,7 +390,9 @@ int qcldpc_autotune_shapes(const qcldpc_code *code, int n_frames, void *workspac
 
 /*
  * Measurement helper; the paper has no counterpart. Replays the check-node
- * pass and then the variable-node pass of the decoder `reps` times each, with
+ * pass and then the variable-node pass of the decoder (with vn_pass = 0 the
+ * light pass that turns the accumulated sums into posteriors) `reps` times
+ * each, with
  * the launch configuration qcldpc_decode uses, on the state a previous
  * qcldpc_decode / qcldpc_decode_soft call with the same code, n_frames and
  * workspace left behind, and returns each pass's mean duration in

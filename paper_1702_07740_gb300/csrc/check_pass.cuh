@@ -191,10 +191,10 @@ __device__ __forceinline__ uint32_t stage_bytes(const void *src, uint32_t count,
 // device error (decoding stops with converged = -1), waits once more
 // (bounded) for its copies, and reports failure.
 __device__ __forceinline__ bool stage_wait(uint64_t *bar, const Work &W) {
-    for (unsigned it = 0; it < kWaitLimit; it++)
+    for (unsigned it = 0; it < W.wait_polls; it++)
         if (mbar_try_wait(bar, 0)) return true;
     atomicOr(W.err, 1);
-    for (unsigned it = 0; it < kWaitLimit; it++)
+    for (unsigned it = 0; it < W.wait_polls; it++)
         if (mbar_try_wait(bar, 0)) break;
     return false;
 }
@@ -520,7 +520,7 @@ __device__ __forceinline__ bool cn_tile(const Table &T, const Work &W, int f, in
             for (int k = 0; k < ND; k++)
                 add(bprev + ob[NH + k] + (i0 >> 5), (nv + 31) / 32, 4, word_slots);
         }
-        mbar_expect_tx(bar, total);
+        mbar_expect_tx(bar, total + W.stall_extra);
         for (int q = 0; q < ncopy; q++) bulk_g2s(stage + slot_start[q], src[q], nb[q], bar);
     }
     __syncthreads();  // barrier initialised, offsets published

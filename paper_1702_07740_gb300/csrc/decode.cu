@@ -59,6 +59,7 @@
 // relative after 50 iterations.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -965,6 +966,13 @@ Work make_work(const qcldpc_code *code, const qcldpc_params &p, int F, int max_i
         w.msg_buf = (int64_t)F * T.n_h * T.Z;
     }
     set_accum(code, p, base + lo.acc, w);
+    w.wait_polls = kWaitLimit;
+    if (const char *e = std::getenv("QCLDPC_TEST_STALL")) {
+        if (e[0] == '1') {  // test switch: every staged wait runs out after a few polls
+            w.wait_polls = 64;
+            w.stall_extra = 16;
+        }
+    }
     return w;
 }
 
@@ -1828,6 +1836,7 @@ extern "C" int qcldpc_pool_create(const qcldpc_code *code_c, int n_slots, int ma
     w.cn_nt = p.cn_threads;
     w.vn_vpt = p.vn_nodes;
     w.vn_split = p.vn_split;
+    w.wait_polls = kWaitLimit;
     if (layered) {
         w.layered = 1;
         w.ngroups = p.layers > 0 ? p.layers : code->tab.mb;

@@ -167,6 +167,12 @@ struct Work {
     float acc_scale;       // FP32 / FP16 messages: fixed-point scale 2^k (int8: unused)
     float acc_inv;         // 2^-k, or the int8 quantum (the sum then counts quanta)
     int32_t accum;         // 1: accumulated posteriors; 0: separate summing variable pass
+    // Bounded waits of the staged check pass: polls before giving up, and a
+    // test switch (QCLDPC_TEST_STALL=1 in the environment) under which each
+    // block expects 16 bytes more than it copies, so that its wait runs out
+    // and the decode reports converged = -1 without any fault.
+    uint32_t wait_polls;
+    uint32_t stall_extra;  // bytes expected beyond the copies (0, or 16 under the switch)
 };
 // Kinds of check pass. kPassFlood: flooding iteration t (stop test of t-1
 // when due, then the update). kPassTest: the stop test of iteration t-1

@@ -116,3 +116,36 @@ def test_multi_rejects_bad_arguments():
     with pytest.raises(q.QcldpcError, match="NOMEM"):
         q.qcldpc_decode_multi([code], [x], [s], [1], 10, None, md.keys, md.converged, md.iters,
                               md.workspace, 256)
+
+
+def test_multi_full_size_matches_one_decode_per_code_and_the_oracle():
+    """n = 10^6 frames of the rate-0.02 and rate-0.10 codes in one batched
+    decode: bit-identical to one decode per code, and frame 0 of each code
+    equal to the oracle's flag and iterations after 20 iterations at a
+    converging SNR."""
+    from concurrent.futures import ThreadPoolExecutor
+    max_iter = 20
+    specs = [(synth.rate002_code, 20000, 0.16), (synth.rate010_code, 100000, 1.0)]
+    frs, codes, ins = [], [], []
+    for i, (mk, Z, snr) in enumerate(specs):
+        fr = make_frames(mk(Z), snr, 2, seed0=9700 + 100 * i)
+        frs.append(fr)
+        codes.append(q.create_code_from(fr.code_dict))
+        ins.append(_inputs(fr))
+    md = q.MultiDecoder(codes, [2, 2])
+    md.decode([x[0] for x in ins], [x[1] for x in ins], max_iter)
+    torch.cuda.synchronize()
+    for c, fr in enumerate(frs):
+        one = q.Decoder(codes[c], 2)
+        one.decode(ins[c][0], ins[c][1], max_iter)
+        torch.cuda.synchronize()
+        assert torch.equal(md.keys[c][: one.keys.numel()], one.keys)
+        assert torch.equal(md.iters[c][:2], one.iters) and torch.equal(md.converged[c][:2], one.converged)
+    with ThreadPoolExecutor(max_workers=2) as ex:
+        refs = list(ex.map(lambda fr: oracle.decode(fr.code, fr.q64[0], fr.syn[0], max_iter), frs))
+    for c, (fr, (_, chat, it, cv)) in enumerate(zip(frs, refs)):
+        conv, its = int(md.converged[c][0]), int(md.iters[c][0])
+        assert (its, conv) == (it, int(cv)), c
+        if cv:
+            keys = _unpack(md.keys[c], 2, fr.code.k)
+            np.testing.assert_array_equal(keys[0], chat[: fr.code.k])

@@ -464,3 +464,24 @@ def test_launch_shapes_give_identical_bits_and_autotune_picks_the_fastest():
     for bad in (dict(cn_threads=48), dict(cn_threads=512), dict(vn_nodes=4), dict(vn_split=3)):
         with pytest.raises(q.QcldpcError, match="INVAL"):
             decode_soft(code, llr, fr.syn, fr.F, iters, **bad)
+
+
+def test_a_staged_wait_that_runs_out_fails_the_decode_without_a_fault(monkeypatch):
+    """Failure detection on the device, without a fault: under the library's
+    test switch every check-pass block expects 16 bytes more than its bulk
+    copies deliver, so its bounded mbarrier wait runs out. The blocks set the
+    device error word and return; the decode stops every frame with
+    converged = -1, and the context stays usable: the next decode matches
+    the oracle."""
+    fr = make_frames(synth.rate002_code(512), 0.05, 2)
+    code = q.create_code_from(fr.code_dict)
+    llr = gpu_llr(fr)
+    monkeypatch.setenv("QCLDPC_TEST_STALL", "1")
+    keys, conv, its, post = decode_soft(code, llr, fr.syn, fr.F, 10)
+    assert (conv == -1).all() and (its == 0).all()
+    monkeypatch.delenv("QCLDPC_TEST_STALL")
+    keys, conv, its, post = decode_soft(code, llr, fr.syn, fr.F, 10, et_start=11)
+    for f in range(fr.F):
+        ref, _, it, cv = oracle.decode(fr.code, fr.q64[f], fr.syn[f], 10, et_start=11)
+        assert its[f] == it and conv[f] == int(cv)
+        assert_posteriors_close(post[f], ref, f"frame {f} after the failed decode")
