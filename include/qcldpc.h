@@ -204,6 +204,16 @@ typedef struct qcldpc_params {
                             1: a separate variable pass re-reads every message
                             and adds them in FP32 (vn_nodes and vn_split
                             apply). Layered decoding ignores it */
+    int32_t frame_groups; /* graph launches (launch_mode 0) of flooding
+                            decodes without soft output: the frames are split
+                            into this many groups of consecutive frames, each
+                            iterating in its own chain of passes inside the
+                            one decode graph; a group's short per-iteration
+                            steps (stop test, posterior pass) run at high
+                            priority, while other groups' check passes fill
+                            the GPU. 0 (default): 2 groups when n_frames >= 2;
+                            1: one chain; at most QCLDPC_MULTI_MAX_CODES (and
+                            at most n_frames). No result bit depends on it */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);
@@ -236,8 +246,12 @@ size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
  *   workspace_dev  DEVICE scratch of at least qcldpc_decode_workspace()
  *                  bytes, 256-byte aligned; contents are overwritten
  * Enqueues on `stream`; returns without waiting. Concurrent calls on one code
- * handle are serialised on the host. Errors: QCLDPC_E_INVAL, _ALIGN, _NOMEM
- * (workspace too small), _CUDA.
+ * handle are serialised on the host. By default (p->frame_groups = 0) a
+ * graph-launched flooding decode of n_frames >= 2 runs its frames as two
+ * groups of consecutive frames in side-by-side chains of one graph (the
+ * instantiated graphs of recent argument sets are kept); the workspace
+ * size accounts for it. Errors: QCLDPC_E_INVAL, _ALIGN, _NOMEM (workspace
+ * too small), _CUDA.
  */
 int qcldpc_decode(const qcldpc_code *code, const float *llr_dev,
                   const uint32_t *syn_dev, int n_frames, int max_iter,

@@ -166,6 +166,7 @@ extern "C" void qcldpc_params_init(qcldpc_params *p) {
     p->vn_nodes = 0;
     p->vn_split = 0;
     p->vn_pass = 0;
+    p->frame_groups = 0;
 }
 
 extern "C" int qcldpc_create_code(int mb, int nb, int Z, int n_circ,

@@ -753,6 +753,20 @@ cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode
     return cudaGraphAddKernelNode(node, g, dep, ndep, &kp);
 }
 
+// Graph node priority of the short per-iteration steps (control, posterior
+// or variable pass): the highest the device offers, so that when several
+// chains share a graph those steps' blocks are scheduled ahead of the
+// pending blocks of another chain's check pass (the graphs are instantiated
+// with cudaGraphInstantiateFlagUseNodePriority).
+cudaError_t raise_priority(cudaGraphNode_t node) {
+    int least = 0, greatest = 0;
+    cudaError_t err = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (err != cudaSuccess) return err;
+    cudaLaunchAttributeValue v = {};
+    v.priority = greatest;
+    return cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &v);
+}
+
 // Loop body of the decode graph. Flooding: check pass -> control ->
 // variable pass. Layered: stop-test pass -> control -> for every row group,
 // its check pass -> its posterior update.
@@ -797,7 +811,9 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
                 const VnLaunch vl = vn_launch(T, F, w0.fmt, w0.vn_vpt, w0.vn_split);
                 err = add_kernel(&n_vn, body, &n_ctrl, 1, vl.func, vl.grid, dim3(kThreads), vn_args, 0, true);
             }
-            if (err != cudaSuccess) return err;
+            if (err != cudaSuccess || (err = raise_priority(n_ctrl)) != cudaSuccess ||
+                (err = raise_priority(n_vn)) != cudaSuccess)
+                return err;
             prev = n_vn;
             continue;
         }
@@ -856,7 +872,7 @@ int build_graph(const qcldpc_code *code, GraphEntry &ge, const Work &w0) {
                           dim3(kThreads), args)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: add output kernel");
     cudaGraphExec_t exec = nullptr;
-    if ((err = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess)
+    if ((err = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority)) != cudaSuccess)
         return qc::cuda_fail(err, "decode: cudaGraphInstantiate");
     ge.exec = exec;
     ge.key = w0;
@@ -976,6 +992,30 @@ Work make_work(const qcldpc_code *code, const qcldpc_params &p, int F, int max_i
     return w;
 }
 
+// Frame groups of a decode (qcldpc_params.frame_groups): graph launches of
+// flooding decodes without soft output run groups of consecutive frames as
+// side-by-side chains of one graph (as qcldpc_decode_multi does for several
+// codes), so that one group's short per-iteration steps overlap another
+// group's check pass; every frame's arithmetic is the same in any group.
+int frame_groups_of(const qcldpc_params &p, int F, bool soft) {
+    if (p.launch_mode != 0 || p.schedule != 0 || soft || F < 2) return 1;
+    return std::min(p.frame_groups > 0 ? p.frame_groups : 2, F);
+}
+// First frame of group g (the groups differ by at most one frame).
+int group_first(int F, int G, int g) { return g * (F / G) + std::min(g, F % G); }
+// Workspace of a grouped decode: the groups' own layouts one after the
+// other (each 256-byte aligned), and at least one layout of all F frames
+// (qcldpc_time_passes replays the passes of the whole batch on it).
+size_t groups_workspace(const Table &T, int F, int G, int fmt) {
+    size_t off = 0;
+    for (int g = 0; g < G; g++)
+        off = align_up(off, 256) +
+              layout_of(T, group_first(F, G, g + 1) - group_first(F, G, g), false, fmt).total;
+    return std::max(off, layout_of(T, F, false, fmt).total);
+}
+int launch_multi(const std::vector<const qcldpc_code *> &used, const std::vector<Work> &works,
+                 cudaStream_t stream);
+
 int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn, int F,
                 int max_iter, const qcldpc_params *p_in, uint32_t *keys, int32_t *conv,
                 int32_t *iters, float *post, void *ws, size_t ws_bytes, cudaStream_t stream) {
@@ -990,19 +1030,20 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     if (max_iter < 0) return fail(QCLDPC_E_INVAL, "decode: max_iter must be >= 0");
     if (!(p.phi_floor > 0.0f) || p.schedule < 0 || p.schedule > 1 || p.msg_format < 0 ||
         p.msg_format > 2 || !(p.msg_step >= 0.0f) || (p.launch_mode != 0 && p.launch_mode != 1) ||
-        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)) || !shape_ok(p))
+        (p.schedule == 1 && (p.layers < 0 || p.layers > code->tab.mb)) || !shape_ok(p) ||
+        p.frame_groups < 0 || p.frame_groups > QCLDPC_MULTI_MAX_CODES)
         return fail(QCLDPC_E_INVAL,
                     "decode: unsupported option (phi_floor > 0, schedule 0..1, layers 0..mb, "
-                    "msg_format 0..2, msg_step >= 0, launch shapes)");
+                    "msg_format 0..2, msg_step >= 0, launch shapes, frame_groups 0..16)");
     if (soft && p.soft_output != 1)
         return fail(QCLDPC_E_INVAL, "decode_soft: params->soft_output must be 1");
     if (F == 0) return QCLDPC_OK;
     if (!llr || !syn || !keys || !conv || !iters || !ws)
         return fail(QCLDPC_E_INVAL, "decode: NULL buffer");
     if (!aligned(ws, 256)) return fail(QCLDPC_E_ALIGN, "decode: workspace must be 256-byte aligned");
-    if (!aligned(llr, 4) || !aligned(syn, 4) || !aligned(keys, 4) || !aligned(conv, 4) ||
+    if (!aligned(llr, 16) || !aligned(syn, 4) || !aligned(keys, 4) || !aligned(conv, 4) ||
         !aligned(iters, 4) || (post && !aligned(post, 4)))
-        return fail(QCLDPC_E_ALIGN, "decode: buffers must be 4-byte aligned");
+        return fail(QCLDPC_E_ALIGN, "decode: LLRs must be 16-byte aligned, other buffers 4-byte aligned");
     int dev = -1;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return cuda_fail(err, "decode: cudaGetDevice");
@@ -1012,7 +1053,9 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     const Table &T = code->tab;
     const bool layered = p.schedule == 1;
     const Layout lo = layout_of(T, F, soft, p.msg_format, layered);
-    if (ws_bytes < lo.total) return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
+    const int G = frame_groups_of(p, F, soft);
+    if (ws_bytes < (G > 1 ? groups_workspace(T, F, G, p.msg_format) : lo.total))
+        return fail(QCLDPC_E_NOMEM, "decode: workspace too small");
     Work w = make_work(code, p, F, max_iter, llr, syn, keys, conv, iters, post, static_cast<char *>(ws), lo);
 
     std::lock_guard<std::mutex> lock(code->mu);
@@ -1021,6 +1064,24 @@ int decode_impl(const qcldpc_code *code_c, const float *llr, const uint32_t *syn
     code->last_soft = soft ? 1 : 0;
     std::memcpy(code->last_work, &w, sizeof(w));
     if (p.launch_mode == 1) return stream_decode(code, w, stream);
+    if (G > 1) {
+        // group g: frames group_first(g) .. group_first(g + 1) - 1, with
+        // its own workspace part (the first layout(F) bytes hold the
+        // whole-batch layout of w only for qcldpc_time_passes)
+        std::vector<const qcldpc_code *> used((size_t)G, code);
+        std::vector<Work> works;
+        size_t off = 0;
+        for (int g = 0; g < G; g++) {
+            const int f0 = group_first(F, G, g), Fg = group_first(F, G, g + 1) - f0;
+            const Layout lg = layout_of(T, Fg, false, p.msg_format);
+            off = align_up(off, 256);
+            works.push_back(make_work(code, p, Fg, max_iter, llr + (size_t)f0 * w.n, syn + (size_t)f0 * w.words_m,
+                                      keys + (size_t)f0 * w.words_k, conv + f0, iters + f0, nullptr,
+                                      static_cast<char *>(ws) + off, lg));
+            off += lg.total;
+        }
+        return launch_multi(used, works, stream);
+    }
 
     GraphCache *gc = static_cast<GraphCache *>(code->graph_cache);
     if (!gc) {
@@ -1067,6 +1128,11 @@ extern "C" size_t qcldpc_decode_workspace(const qcldpc_code *code, int n_frames,
     const bool soft = p && p->soft_output == 1;
     const int fmt = p ? p->msg_format : 0;
     if (fmt < 0 || fmt > 2) return 0;
+    qcldpc_params d;
+    qcldpc_params_init(&d);
+    if (p && (p->frame_groups < 0 || p->frame_groups > QCLDPC_MULTI_MAX_CODES)) return 0;
+    const int G = frame_groups_of(p ? *p : d, n_frames, soft);
+    if (G > 1) return groups_workspace(code->tab, n_frames, G, fmt);
     return layout_of(code->tab, n_frames, soft, fmt, p && p->schedule == 1).total;
 }
 
@@ -1132,7 +1198,9 @@ struct MultiDecodeGraph {
     std::vector<Work> works;
     unsigned long long stamp = 0;
 };
-constexpr int kMultiDecodeGraphs = 8;
+// Batched decode graphs kept instantiated (least recently used replaced):
+// qcldpc_decode_multi's and the grouped single-code decodes' argument sets.
+constexpr int kMultiDecodeGraphs = 32;
 std::mutex g_mdec_mu;
 MultiDecodeGraph g_mdec[kMultiDecodeGraphs];
 unsigned long long g_mdec_clock = 0;
@@ -1200,7 +1268,7 @@ int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code 
             return qc::cuda_fail(err, "decode_multi: add output kernel");
     }
     cudaGraphExec_t exec = nullptr;
-    if ((err = cudaGraphInstantiate(&exec, g, 0)) != cudaSuccess)
+    if ((err = cudaGraphInstantiate(&exec, g, cudaGraphInstantiateFlagUseNodePriority)) != cudaSuccess)
         return qc::cuda_fail(err, "decode_multi: cudaGraphInstantiate");
     ge.exec = exec;
     ge.codes = codes;
@@ -1210,6 +1278,34 @@ int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code 
 
 // Validated options of a batched decode (flooding, hard output, FP32 / FP16 /
 // int8 storage, launch shapes chosen by the library per code).
+// Launch the batched decode graph of (codes, works), from the cache of
+// recent argument sets or built and instantiated now.
+int launch_multi(const std::vector<const qcldpc_code *> &used, const std::vector<Work> &works,
+                 cudaStream_t stream) {
+    using namespace qc;
+    std::lock_guard<std::mutex> lock(g_mdec_mu);
+    MultiDecodeGraph *hit = nullptr, *victim = &g_mdec[0];
+    for (auto &g : g_mdec) {
+        if (g.exec && g.codes == used && g.works.size() == works.size() &&
+            std::memcmp(g.works.data(), works.data(), sizeof(Work) * works.size()) == 0)
+            hit = &g;
+        if (!g.exec || (victim->exec && g.stamp < victim->stamp)) victim = &g;
+    }
+    if (!hit) {
+        free_multi(*victim);
+        if (int st = build_multi_graph(*victim, used, works)) {
+            free_multi(*victim);
+            return st;
+        }
+        hit = victim;
+    }
+    hit->stamp = ++g_mdec_clock;
+    cudaError_t err = cudaGraphLaunch(hit->exec, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "decode_multi: cudaGraphLaunch");
+    clear_error();
+    return QCLDPC_OK;
+}
+
 bool multi_params_ok(const qcldpc_params &p) {
     return p.phi_floor > 0.0f && p.schedule == 0 && p.soft_output == 0 && p.msg_format >= 0 &&
            p.msg_format <= 2 && p.msg_step >= 0.0f && shape_ok(p);
@@ -1286,27 +1382,7 @@ extern "C" int qcldpc_decode_multi(int n_codes, const qcldpc_code *const *codes,
     }
     if (workspace_bytes < off) return fail(QCLDPC_E_NOMEM, "decode_multi: workspace too small");
     if (used.empty()) return QCLDPC_OK;
-    std::lock_guard<std::mutex> lock(g_mdec_mu);
-    MultiDecodeGraph *hit = nullptr, *victim = &g_mdec[0];
-    for (auto &g : g_mdec) {
-        if (g.exec && g.codes == used && g.works.size() == works.size() &&
-            std::memcmp(g.works.data(), works.data(), sizeof(Work) * works.size()) == 0)
-            hit = &g;
-        if (!g.exec || (victim->exec && g.stamp < victim->stamp)) victim = &g;
-    }
-    if (!hit) {
-        free_multi(*victim);
-        if (int st = build_multi_graph(*victim, used, works)) {
-            free_multi(*victim);
-            return st;
-        }
-        hit = victim;
-    }
-    hit->stamp = ++g_mdec_clock;
-    if ((err = cudaGraphLaunch(hit->exec, (cudaStream_t)stream)) != cudaSuccess)
-        return cuda_fail(err, "decode_multi: cudaGraphLaunch");
-    clear_error();
-    return QCLDPC_OK;
+    return launch_multi(used, works, (cudaStream_t)stream);
 }
 
 extern "C" int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev,

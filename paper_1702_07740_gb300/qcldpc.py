@@ -58,6 +58,7 @@ class qcldpc_params(ctypes.Structure):
         ("vn_nodes", ctypes.c_int32),
         ("vn_split", ctypes.c_int32),
         ("vn_pass", ctypes.c_int32),
+        ("frame_groups", ctypes.c_int32),
     ]
 
 

@@ -149,3 +149,56 @@ def test_multi_full_size_matches_one_decode_per_code_and_the_oracle():
         if cv:
             keys = _unpack(md.keys[c], 2, fr.code.k)
             np.testing.assert_array_equal(keys[0], chat[: fr.code.k])
+
+
+@pytest.mark.parametrize("fmt", [0, 1, 2])
+def test_frame_groups_equal_one_chain(fmt):
+    """A flooding decode whose frames run as side-by-side groups (the
+    default for >= 2 frames) gives every frame the key bits, flag and stop
+    iteration of the one-chain decode: 2, 3 and one-frame groups, ragged
+    group sizes, with and without delayed early termination."""
+    max_iter = 40
+    d = synth.rate002_code(64)
+    fr = make_frames(d, 0.05, 7, seed0=9800)  # the oracle converges 5 of 7 in 40 iterations
+    code = q.create_code_from(fr.code_dict)
+    llr, syn = _inputs(fr)
+    for et in (1, 12):
+        ref = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=1))
+        ref.decode(llr, syn, max_iter)
+        torch.cuda.synchronize()
+        if fmt == 0:
+            assert 0 < int(ref.converged.sum()) < fr.F
+        for G in (0, 3, 7):
+            dec = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=G))
+            dec.decode(llr, syn, max_iter)
+            torch.cuda.synchronize()
+            assert torch.equal(dec.keys, ref.keys), (et, G)
+            assert torch.equal(dec.converged, ref.converged), (et, G)
+            assert torch.equal(dec.iters, ref.iters), (et, G)
+
+
+def test_frame_groups_full_size_equal_one_chain():
+    """n = 10^6, 5 frames in the default two groups (3 + 2) against one
+    chain, 30 iterations at a converging SNR."""
+    max_iter = 30
+    fr = make_frames(synth.rate002_code(20000), 0.16, 5, seed0=9900)
+    code = q.create_code_from(fr.code_dict)
+    llr, syn = _inputs(fr)
+    out = []
+    for G in (1, 0):
+        dec = q.Decoder(code, fr.F, q.qcldpc_params_init(frame_groups=G))
+        dec.decode(llr, syn, max_iter)
+        torch.cuda.synchronize()
+        out.append((dec.keys.clone(), dec.converged.clone(), dec.iters.clone()))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
+def test_frame_groups_rejects_out_of_range():
+    code = q.create_code_from(synth.rate002_code(64))
+    dec = q.Decoder(code, 2)
+    x = torch.zeros(2 * code.n, device="cuda")
+    s = torch.zeros(2 * ((code.m + 31) // 32), dtype=torch.int32, device="cuda")
+    with pytest.raises(q.QcldpcError, match="INVAL"):
+        q.qcldpc_decode(code, x, s, 2, 10, q.qcldpc_params_init(frame_groups=17), dec.keys,
+                        dec.converged, dec.iters, dec.workspace, dec.ws_bytes)
