@@ -69,6 +69,9 @@ def parse_args():
     ap.add_argument("--vn-pass", choices=["accumulate", "separate"], default="accumulate",
                     help="flooding posteriors: integer sums accumulated by the check pass, or a "
                          "separate variable pass re-reading every message")
+    ap.add_argument("--frame-groups", type=int, default=0,
+                    help="flooding graph decodes: side-by-side frame groups (0 = library choice, "
+                         "1 = one chain)")
     ap.add_argument("--layers", type=int, default=0,
                     help="layered: row groups per iteration (0 = one per base row)")
     ap.add_argument("--study", choices=["fer", "batch", "serve", "schedule", "et"], default=None,
@@ -221,6 +224,13 @@ def iteration_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_byte
             + (mb * Z + 2 * n_d1 * Z) / 8)
 
 
+def groups_of(args, F):
+    """Frame groups the decode runs as (the library's rule for frame_groups)."""
+    if args.launch_mode != "graph" or args.schedule != "flooding" or F < 2:
+        return 1
+    return min(args.frame_groups or 2, F)
+
+
 def source_hash():
     """Hash of the decoder's kernel sources with comments and blank space
     removed: the committed DRAM counters stay valid across comment edits and
@@ -369,7 +379,8 @@ def run_ours(args, world, rank, local):
                                   msg_format={"fp32": 0, "fp16": 1, "int8": 2}[args.msg_format],
                                   schedule=1 if args.schedule == "layered" else 0,
                                   layers=args.layers,
-                                  vn_pass=0 if args.vn_pass == "accumulate" else 1)
+                                  vn_pass=0 if args.vn_pass == "accumulate" else 1,
+                                  frame_groups=args.frame_groups)
     layered = args.schedule == "layered"
 
     # --- seeded inputs, resident in HBM before timing
@@ -570,6 +581,7 @@ def run_ours(args, world, rank, local):
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "msg_format": args.msg_format, "vn_pass": args.vn_pass if not layered else None,
+        "frame_groups": groups_of(args, F),
         "schedule": args.schedule if not layered else f"layered, {args.layers or d['mb']} row groups",
         "config": {"workload": WORKLOAD if args.code == "rate002" else
                    "met_rate0.02_n1e6_snr%g_max%dit_%dframes" % (args.snr, args.max_iter, F),

@@ -1809,6 +1809,9 @@ cudaError_t add_pool_passes(cudaGraph_t g, const qcldpc_pool *pool, int n_passes
                 else
                     err = add_kernel(&c, g, &b, 1, vl.func, vl.grid, dim3(kThreads), vn_args);
             }
+            // the short steps ahead of other pools' pending check blocks
+            if (err == cudaSuccess) err = raise_priority(b);
+            if (err == cudaSuccess) err = raise_priority(c);
             prev = c;
             continue;
         }
@@ -2010,7 +2013,8 @@ extern "C" int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_p
             cudaGraphNode_t last;
             if ((err = add_pool_passes(hit->graph, pool, n_passes, &last)) != cudaSuccess)
                 return cuda_fail(err, "pools_step: add passes");
-            if ((err = cudaGraphInstantiate(&hit->exec, hit->graph, 0)) != cudaSuccess) {
+            if ((err = cudaGraphInstantiate(&hit->exec, hit->graph, cudaGraphInstantiateFlagUseNodePriority)) !=
+                cudaSuccess) {
                 hit->exec = nullptr;
                 return cuda_fail(err, "pools_step: cudaGraphInstantiate");
             }
@@ -2041,7 +2045,8 @@ extern "C" int qcldpc_pools_step(int n_pools, qcldpc_pool *const *pools, int n_p
             cudaGraphNode_t last;
             err = add_pool_passes(hit->graph, pools[i], n_passes, &last);
         }
-        if (err == cudaSuccess) err = cudaGraphInstantiate(&hit->exec, hit->graph, 0);
+        if (err == cudaSuccess)
+            err = cudaGraphInstantiate(&hit->exec, hit->graph, cudaGraphInstantiateFlagUseNodePriority);
         if (err != cudaSuccess) {
             hit->exec = nullptr;
             return cuda_fail(err, "pools_step: build graph");
