@@ -248,11 +248,13 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(pass_name: str, code: str, msg_format: str, frames: int):
+def ncu_traffic(pass_name: str, code: str, msg_format: str, frames: int, schedule: str = "flooding",
+                vn_pass: str = "accumulate"):
     """(kernel name, per-launch DRAM bytes) of a decoder pass on a code from
     the committed ncu summary (entries keyed "<code>:<pass>"), or (None,
     None) when the kernel source changed since the capture or the capture was
-    of another configuration."""
+    of another configuration (code, storage, frames, schedule, posterior
+    form)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -261,7 +263,8 @@ def ncu_traffic(pass_name: str, code: str, msg_format: str, frames: int):
         return None, None
     e = d.get(f"{code}:{pass_name}")
     if (not e or e.get("source_hash") != source_hash() or e.get("msg_format", "fp32") != msg_format
-            or e.get("frames") != frames):
+            or e.get("frames") != frames or e.get("schedule", "flooding") != schedule
+            or e.get("vn_pass", "accumulate") != vn_pass):
         return None, None
     return e.get("kernel"), e.get("dram_bytes_per_launch")
 
@@ -452,19 +455,25 @@ def run_ours(args, world, rank, local):
     # --- accuracy and launch count (deterministic: a batch decodes identically each time)
     frame_err = conv_n = 0
     iters_all = []
-    loop_passes = []
-    for b in range(B):
+    # statistics over the batches the timed steps decoded (fewer steps than
+    # batches leave some undecoded)
+    used = sorted({s % B for s in range(args.steps)})
+    loop_passes = [0] * B
+    for b in used:
         keys = synth.unpack_bits(batches[b]["keys"].cpu().numpy().view(np.uint32).reshape(F, wk), k)
         conv = batches[b]["conv"].cpu().numpy()
         its = batches[b]["iters"].cpu().numpy()
         frame_err += int((keys != host[b]["key_ref"]).any(axis=1).sum())
         conv_n += int(conv.sum())
         iters_all.extend(its.tolist())
-        loop_passes.append(int(its.max()) + 1)
-    frames_total = B * F
+        loop_passes[b] = int(its.max()) + 1
+    frames_total = len(used) * F
     fer = frame_err / frames_total
-    # per step: llr + init + final, and per loop pass check pass + control +
-    # variable pass (flooding) or test pass + control + 2 per row group (layered)
+    # per step: llr, and per frame group init + final; per loop pass and
+    # group check pass + control + variable pass (flooding) or test pass +
+    # control + 2 per row group (layered); with several groups, one join
+    # kernel per trip sets the loop condition
+    G = groups_of(args, F)
     per_pass = 2 + 2 * (args.layers or d["mb"]) if layered else 3
     # the decode graph runs flooding iterations four per trip of its loop,
     # and the stream launch mode enqueues max_iter + 1 passes; passes after
@@ -472,7 +481,8 @@ def run_ours(args, world, rank, local):
     if args.launch_mode == "stream":
         loop_passes = [args.max_iter + 1] * B
     unroll = 4 if (not layered and args.launch_mode != "stream") else 1
-    launches = sum(3 + per_pass * -(-loop_passes[s % B] // unroll) * unroll for s in range(args.steps))
+    trips = [-(-loop_passes[s % B] // unroll) for s in range(args.steps)]
+    launches = sum(1 + 2 * G + t * (G * per_pass * unroll + (1 if G > 1 else 0)) for t in trips)
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host.
     # Two staging buffers and a copy stream: the inputs of step s+1 are copied
@@ -550,8 +560,11 @@ def run_ours(args, world, rank, local):
                               else ("variable_pass", vn_ms, vn_b * F))
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     peak = float(peaks["hbm_gbs"])
-    kname, traffic = ncu_traffic(dom, args.code, args.msg_format, F)
-    iter_ms = cn_ms + vn_ms
+    kname, traffic = ncu_traffic(dom, args.code, args.msg_format, F, args.schedule, args.vn_pass)
+    # device time per loop iteration of the timed decode (its llr, init and
+    # final kernels included): the frame groups overlap passes, so this is
+    # below the single-kernel replays' cn_ms + vn_ms
+    iter_ms = elapsed * 1e3 / sum(loop_passes[s % B] for s in range(args.steps))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
