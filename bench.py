@@ -225,10 +225,11 @@ def iteration_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_byte
 
 
 def groups_of(args, F):
-    """Frame groups the decode runs as (the library's rule for frame_groups)."""
-    if args.launch_mode != "graph" or args.schedule != "flooding" or F < 2:
+    """Frame groups the decode runs as (the library's rule for frame_groups:
+    by default two for flooding, one chain for layered decoding)."""
+    if args.launch_mode != "graph" or F < 2:
         return 1
-    return min(args.frame_groups or 2, F)
+    return min(args.frame_groups or (2 if args.schedule == "flooding" else 1), F)
 
 
 def source_hash():

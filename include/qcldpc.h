@@ -204,16 +204,20 @@ typedef struct qcldpc_params {
                             1: a separate variable pass re-reads every message
                             and adds them in FP32 (vn_nodes and vn_split
                             apply). Layered decoding ignores it */
-    int32_t frame_groups; /* graph launches (launch_mode 0) of flooding
-                            decodes without soft output: the frames are split
-                            into this many groups of consecutive frames, each
+    int32_t frame_groups; /* graph launches (launch_mode 0) of decodes
+                            without soft output: the frames are split into
+                            this many groups of consecutive frames, each
                             iterating in its own chain of passes inside the
-                            one decode graph; a group's short per-iteration
-                            steps (stop test, posterior pass) run at high
-                            priority, while other groups' check passes fill
-                            the GPU. 0 (default): 2 groups when n_frames >= 2;
-                            1: one chain; at most QCLDPC_MULTI_MAX_CODES (and
-                            at most n_frames). No result bit depends on it */
+                            one decode graph. Flooding: a group's short
+                            per-iteration steps (stop test, posterior pass)
+                            run at high priority while other groups' check
+                            passes fill the GPU; layered: the groups' small
+                            per-row-group passes run side by side. 0
+                            (default): 2 groups for flooding when n_frames
+                            >= 2, one chain for layered decoding (its many
+                            small launches gain less than they cost); 1: one
+                            chain; at most QCLDPC_MULTI_MAX_CODES (and at
+                            most n_frames). No result bit depends on it */
 } qcldpc_params;
 
 void qcldpc_params_init(qcldpc_params *p);

@@ -81,7 +81,7 @@ def test_layered_workspace_holds_two_message_buffers():
     d = synth.rate002_code(512)
     code = q.create_code_from(d)
     flood = q.qcldpc_decode_workspace(code, 3, q.qcldpc_params_init(frame_groups=1))
-    lay = q.qcldpc_decode_workspace(code, 3, q.qcldpc_params_init(schedule=1))
+    lay = q.qcldpc_decode_workspace(code, 3, q.qcldpc_params_init(schedule=1, frame_groups=1))
     n_h, n_hcols = 119, 2
     acc = -(-4 * (3 * n_hcols * 2 * 512 + 4096) // 256) * 256
     assert lay - flood >= 3 * n_h * 512 * 4 - acc - 256
@@ -89,27 +89,32 @@ def test_layered_workspace_holds_two_message_buffers():
 
 
 def test_grouped_flooding_workspace_holds_each_group_and_the_whole_batch():
-    """Flooding decodes of >= 2 frames run as frame groups by default: the
-    workspace holds every group's own layout (256-byte aligned, one after
-    the other) and at least one layout of the whole batch; one frame, a
-    layered decode, soft output or frame_groups = 1 keep one layout; a group
-    count beyond 16 is invalid."""
+    """Grouped decodes (by default flooding with >= 2 frames; layered when
+    frame_groups asks for groups): the workspace holds every group's own
+    layout (256-byte aligned, one after the other) and at least one layout
+    of the whole batch; one frame, stream launches, soft output, a default
+    layered decode or frame_groups = 1 keep one layout; a group count beyond
+    16 is invalid."""
     code = q.create_code_from(synth.rate002_code(512))
-    one = lambda F: q.qcldpc_decode_workspace(code, F, q.qcldpc_params_init(frame_groups=1))
     align = lambda x: -(-x // 256) * 256
-    for F, G in [(2, 2), (3, 2), (16, 2), (5, 4), (16, 16)]:
-        groups = [F // G + (g < F % G) for g in range(G)]
-        parts = 0
-        for Fg in groups:
-            parts = align(parts) + one(Fg)
-        got = q.qcldpc_decode_workspace(code, F, q.qcldpc_params_init(frame_groups=G if G != 2 else 0))
-        assert got == max(parts, one(F)), (F, G)
-        assert got >= one(F)
-    assert q.qcldpc_decode_workspace(code, 1) == one(1)
+    for sched in (0, 1):
+        one = lambda F: q.qcldpc_decode_workspace(code, F, q.qcldpc_params_init(schedule=sched, frame_groups=1))
+        for F, G in [(2, 2), (3, 2), (16, 2), (5, 4), (16, 16)]:
+            groups = [F // G + (g < F % G) for g in range(G)]
+            parts = 0
+            for Fg in groups:
+                parts = align(parts) + one(Fg)
+            p = q.qcldpc_params_init(schedule=sched, frame_groups=G if (G != 2 or sched) else 0)
+            got = q.qcldpc_decode_workspace(code, F, p)
+            assert got == max(parts, one(F)), (sched, F, G)
+            assert got >= one(F)
+        assert q.qcldpc_decode_workspace(code, 1, q.qcldpc_params_init(schedule=sched)) == one(1)
+    lay1 = q.qcldpc_decode_workspace(code, 6, q.qcldpc_params_init(schedule=1, frame_groups=1))
+    assert q.qcldpc_decode_workspace(code, 6, q.qcldpc_params_init(schedule=1)) == lay1
     assert q.qcldpc_decode_workspace(code, 7, q.qcldpc_params_init(frame_groups=9)) == \
         q.qcldpc_decode_workspace(code, 7, q.qcldpc_params_init(frame_groups=7))
-    for p in (q.qcldpc_params_init(schedule=1), q.qcldpc_params_init(launch_mode=1)):
-        p1 = q.qcldpc_params_init(schedule=p.schedule, launch_mode=p.launch_mode, frame_groups=1)
+    for p in (q.qcldpc_params_init(launch_mode=1), q.qcldpc_params_init(soft_output=1)):
+        p1 = q.qcldpc_params_init(launch_mode=p.launch_mode, soft_output=p.soft_output, frame_groups=1)
         assert q.qcldpc_decode_workspace(code, 6, p) == q.qcldpc_decode_workspace(code, 6, p1)
     assert q.qcldpc_decode_workspace(code, 6, q.qcldpc_params_init(frame_groups=17)) == 0
     assert q.qcldpc_decode_workspace(code, 6, q.qcldpc_params_init(frame_groups=-1)) == 0

@@ -151,25 +151,27 @@ def test_multi_full_size_matches_one_decode_per_code_and_the_oracle():
             np.testing.assert_array_equal(keys[0], chat[: fr.code.k])
 
 
-@pytest.mark.parametrize("fmt", [0, 1, 2])
-def test_frame_groups_equal_one_chain(fmt):
-    """A flooding decode whose frames run as side-by-side groups (the
-    default for >= 2 frames) gives every frame the key bits, flag and stop
-    iteration of the one-chain decode: 2, 3 and one-frame groups, ragged
-    group sizes, with and without delayed early termination."""
+@pytest.mark.parametrize("fmt,layers", [(0, None), (1, None), (2, None), (0, 7), (0, 49)])
+def test_frame_groups_equal_one_chain(fmt, layers):
+    """A decode whose frames run as side-by-side groups (the default for >= 2
+    frames, flooding or layered with `layers` row groups) gives every frame
+    the key bits, flag and stop iteration of the one-chain decode: 2, 3 and
+    one-frame groups, ragged group sizes, with and without delayed early
+    termination."""
     max_iter = 40
     d = synth.rate002_code(64)
     fr = make_frames(d, 0.05, 7, seed0=9800)  # the oracle converges 5 of 7 in 40 iterations
     code = q.create_code_from(fr.code_dict)
     llr, syn = _inputs(fr)
+    sched = {} if layers is None else {"schedule": 1, "layers": layers}
     for et in (1, 12):
-        ref = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=1))
+        ref = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=1, **sched))
         ref.decode(llr, syn, max_iter)
         torch.cuda.synchronize()
         if fmt == 0:
             assert 0 < int(ref.converged.sum()) < fr.F
         for G in (0, 3, 7):
-            dec = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=G))
+            dec = q.Decoder(code, fr.F, q.qcldpc_params_init(msg_format=fmt, et_start=et, frame_groups=G, **sched))
             dec.decode(llr, syn, max_iter)
             torch.cuda.synchronize()
             assert torch.equal(dec.keys, ref.keys), (et, G)
