@@ -459,7 +459,10 @@ def run_ours(args, world, rank, local):
     # statistics over the batches the timed steps decoded (fewer steps than
     # batches leave some undecoded)
     used = sorted({s % B for s in range(args.steps)})
+    G = groups_of(args, F)
+    firsts = [g * (F // G) + min(g, F % G) for g in range(G + 1)]  # the library's frame groups
     loop_passes = [0] * B
+    group_passes = [[0] * G for _ in range(B)]  # passes each group's own loop needed
     for b in used:
         keys = synth.unpack_bits(batches[b]["keys"].cpu().numpy().view(np.uint32).reshape(F, wk), k)
         conv = batches[b]["conv"].cpu().numpy()
@@ -468,22 +471,22 @@ def run_ours(args, world, rank, local):
         conv_n += int(conv.sum())
         iters_all.extend(its.tolist())
         loop_passes[b] = int(its.max()) + 1
+        group_passes[b] = [int(its[firsts[g]:firsts[g + 1]].max()) + 1 for g in range(G)]
     frames_total = len(used) * F
     fer = frame_err / frames_total
-    # per step: llr, and per frame group init + final; per loop pass and
-    # group check pass + control + variable pass (flooding) or test pass +
-    # control + 2 per row group (layered); with several groups, one join
-    # kernel per trip sets the loop condition
-    G = groups_of(args, F)
+    # per step: llr, and per frame group init + final; per loop pass of a
+    # group's own loop, check pass + control + variable pass (flooding) or
+    # test pass + control + 2 per row group (layered)
     per_pass = 2 + 2 * (args.layers or d["mb"]) if layered else 3
-    # the decode graph runs flooding iterations four per trip of its loop,
-    # and the stream launch mode enqueues max_iter + 1 passes; passes after
-    # every frame stopped exit at once but still launch
+    # each group's loop runs flooding iterations four per trip until its own
+    # frames have stopped, and the stream launch mode enqueues max_iter + 1
+    # passes; passes after every frame stopped exit at once but still launch
     if args.launch_mode == "stream":
         loop_passes = [args.max_iter + 1] * B
+        group_passes = [[args.max_iter + 1] * G for _ in range(B)]
     unroll = 4 if (not layered and args.launch_mode != "stream") else 1
-    trips = [-(-loop_passes[s % B] // unroll) for s in range(args.steps)]
-    launches = sum(1 + 2 * G + t * (G * per_pass * unroll + (1 if G > 1 else 0)) for t in trips)
+    launches = sum(1 + 2 * G + sum(-(-p // unroll) * unroll * per_pass for p in group_passes[s % B])
+                   for s in range(args.steps))
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host.
     # Two staging buffers and a copy stream: the inputs of step s+1 are copied

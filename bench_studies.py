@@ -7,7 +7,7 @@
   interval, mean iterations and decoded Mbit/s.
 * ``batch``: 256 frames drawn uniformly from nine codes (rates 0.02, 0.05
   and 0.10, each at n = 10^5, 4*10^5 and 10^6) decoded together in one
-  batched decode (one graph launch with a device-side loop over all codes),
+  batched decode (one graph launch, each code in its own device-side loop),
   and by frame pools stepped in one graph launch per step (FP16 and FP32
   messages), against the plain FP32 decoder run one frame at a time and one
   code at a time. Each variant decodes the mix --mix-reps times in a row.

@@ -281,8 +281,9 @@ int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
  * Batched decoding of the frames of several codes in one graph launch (frame
  * batching across codes; the paper decodes one frame of one code per GPU).
  * Code c's n_frames[c] frames run the rule of qcldpc_decode (flooding,
- * Algorithm 1) with their own stop test; one device-side loop runs the
- * passes of all codes side by side until every frame has stopped. The
+ * Algorithm 1) with their own stop test; each code's frames iterate in
+ * their own device-side loop, the loops of all codes side by side in the
+ * one graph (each ends when its own frames have stopped). The
  * results (key bits, flags, iterations) are the ones one qcldpc_decode call
  * per code with the same frames and options returns.
  *

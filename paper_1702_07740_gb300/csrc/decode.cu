@@ -769,13 +769,10 @@ cudaError_t raise_priority(cudaGraphNode_t node) {
 
 // Loop body of the decode graph. Flooding: check pass -> control ->
 // variable pass. Layered: stop-test pass -> control -> for every row group,
-// its check pass -> its posterior update.
-// set_cond: the body's control steps set the loop condition from this
-// code's frames (a one-code decode); otherwise the caller adds a step that
-// sets it. *last (if given) receives the body's last node.
+// its check pass -> its posterior update. The control steps set the loop
+// condition (handle) from the chain's own frames.
 cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline &CI,
-                          const Work &w0, cudaGraphConditionalHandle handle, bool set_cond = true,
-                          cudaGraphNode_t *last = nullptr) {
+                          const Work &w0, cudaGraphConditionalHandle handle) {
     const int F = w0.n_frames;
     Table tcopy = T;
     Work wcopy = w0;
@@ -799,8 +796,7 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
         if ((err = add_kernel(&n_cn, body, prev ? &prev : nullptr, prev ? 1 : 0, cl.func, cl.grid, cl.block,
                               args, cl.smem, prev != nullptr && QCLDPC_PDL_LOOP)) != cudaSuccess)
             return err;
-        if ((err = add_kernel(&n_ctrl, body, &n_cn, 1,
-                              set_cond ? (void *)ctrl_kernel<true> : (void *)ctrl_kernel<false>, dim3(1),
+        if ((err = add_kernel(&n_ctrl, body, &n_cn, 1, (void *)ctrl_kernel<true>, dim3(1),
                               dim3(kCtrlThreads), ctrl_args, 0, pdl)) != cudaSuccess)
             return err;
         if (!w0.layered) {
@@ -835,7 +831,6 @@ cudaError_t add_loop_body(cudaGraph_t body, const Table &T, const qc::ColsInline
             prev = b;
         }
     }
-    if (last) *last = prev;
     return cudaSuccess;
 }
 
@@ -1178,24 +1173,6 @@ namespace {
 
 constexpr int kMultiMaxCodes = QCLDPC_MULTI_MAX_CODES;
 
-struct MultiActive {
-    int32_t n;
-    int32_t frames[kMultiMaxCodes];
-    const int32_t *active[kMultiMaxCodes];
-};
-
-__global__ void __launch_bounds__(kCtrlThreads) multi_cond_kernel(const __grid_constant__ MultiActive A,
-                                                                  cudaGraphConditionalHandle handle) {
-    __shared__ int any;
-    if (threadIdx.x == 0) any = 0;
-    __syncthreads();
-    for (int c = 0; c < A.n; c++)
-        for (int f = threadIdx.x; f < A.frames[c]; f += blockDim.x)
-            if (A.active[c][f]) any = 1;
-    __syncthreads();
-    if (threadIdx.x == 0) cudaGraphSetConditional(handle, any ? 1u : 0u);
-}
-
 struct MultiDecodeGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1219,6 +1196,12 @@ void free_multi(MultiDecodeGraph &g) {
     g.works.clear();
 }
 
+// One graph for several chains of frames (codes of a batched decode, or
+// the frame groups of one code): chain c is init -> its own conditional
+// WHILE loop (whose control steps set its condition from its frames) ->
+// final, and the chains are independent branches. Each chain stops when
+// its own frames have stopped, and the chains never wait for each other
+// inside the loop, so their passes stay interleaved.
 int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code *> &codes,
                       const std::vector<Work> &works) {
     cudaError_t err;
@@ -1226,48 +1209,27 @@ int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code 
     if ((err = cudaGraphCreate(&g, 0)) != cudaSuccess) return qc::cuda_fail(err, "decode_multi: cudaGraphCreate");
     ge.graph = g;
     const int blocks = sm_count() * 4;
-    const int n = (int)codes.size();
-    std::vector<cudaGraphNode_t> inits(n), lasts(n);
-    for (int c = 0; c < n; c++) {
+    for (size_t c = 0; c < codes.size(); c++) {
         Table tcopy = codes[c]->tab;
         Work wcopy = works[c];
         void *args[] = {&tcopy, &wcopy};
-        if ((err = add_kernel(&inits[c], g, nullptr, 0, (void *)init_kernel, dim3(blocks), dim3(kThreads),
+        cudaGraphNode_t n_init, n_cond, n_final;
+        if ((err = add_kernel(&n_init, g, nullptr, 0, (void *)init_kernel, dim3(blocks), dim3(kThreads),
                               args)) != cudaSuccess)
             return qc::cuda_fail(err, "decode_multi: add init node");
-    }
-    cudaGraphConditionalHandle handle;
-    if ((err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode_multi: cudaGraphConditionalHandleCreate");
-    cudaGraphNodeParams cp = {};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = handle;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t n_cond;
-    if ((err = cudaGraphAddNode(&n_cond, g, inits.data(), nullptr, n, &cp)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode_multi: add conditional node");
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    MultiActive A;
-    std::memset(&A, 0, sizeof(A));
-    A.n = n;
-    for (int c = 0; c < n; c++) {
-        if ((err = add_loop_body(body, codes[c]->tab, codes[c]->cols_in, works[c], handle, false, &lasts[c])) !=
-            cudaSuccess)
+        cudaGraphConditionalHandle handle;
+        if ((err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+            return qc::cuda_fail(err, "decode_multi: cudaGraphConditionalHandleCreate");
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = handle;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        if ((err = cudaGraphAddNode(&n_cond, g, &n_init, nullptr, 1, &cp)) != cudaSuccess)
+            return qc::cuda_fail(err, "decode_multi: add conditional node");
+        if ((err = add_loop_body(cp.conditional.phGraph_out[0], codes[c]->tab, codes[c]->cols_in, works[c],
+                                 handle)) != cudaSuccess)
             return qc::cuda_fail(err, "decode_multi: add loop body");
-        A.frames[c] = works[c].n_frames;
-        A.active[c] = works[c].active;
-    }
-    cudaGraphNode_t n_join;
-    void *jargs[] = {&A, &handle};
-    if ((err = add_kernel(&n_join, body, lasts.data(), n, (void *)multi_cond_kernel, dim3(1), dim3(kCtrlThreads),
-                          jargs)) != cudaSuccess)
-        return qc::cuda_fail(err, "decode_multi: add loop condition");
-    for (int c = 0; c < n; c++) {
-        Table tcopy = codes[c]->tab;
-        Work wcopy = works[c];
-        void *args[] = {&tcopy, &wcopy};
-        cudaGraphNode_t n_final;
         if ((err = add_kernel(&n_final, g, &n_cond, 1, (void *)final_kernel, dim3(blocks), dim3(kThreads),
                               args)) != cudaSuccess)
             return qc::cuda_fail(err, "decode_multi: add output kernel");
@@ -1281,8 +1243,6 @@ int build_multi_graph(MultiDecodeGraph &ge, const std::vector<const qcldpc_code 
     return QCLDPC_OK;
 }
 
-// Validated options of a batched decode (flooding, hard output, FP32 / FP16 /
-// int8 storage, launch shapes chosen by the library per code).
 // Launch the batched decode graph of (codes, works), from the cache of
 // recent argument sets or built and instantiated now.
 int launch_multi(const std::vector<const qcldpc_code *> &used, const std::vector<Work> &works,
