@@ -385,9 +385,10 @@ int qcldpc_autotune(const qcldpc_code *code, const float *llr_dev, const uint32_
                     qcldpc_params *best, float *times_ms, qcldpc_stream_t stream);
 
 /*
- * Launch-shape autotuner; the paper has no counterpart. On the state a
- * previous flooding qcldpc_decode / qcldpc_decode_soft call with the same
- * code, n_frames and workspace left behind, replays the check-node pass with
+ * Launch-shape autotuner; the paper has no counterpart. On the workspace of
+ * a previous flooding qcldpc_decode / qcldpc_decode_soft call with the same
+ * code and n_frames (read as qcldpc_time_passes reads it), replays the
+ * check-node pass with
  * blocks of 32, 64, ..., 256 threads, and the separate variable-node pass
  * (the one vn_pass = 1 selects) with (nodes per thread, vn_split) = (1,1),
  * (2,1), (3,1), (1,2), (2,2), (3,2), each `reps` times after one warm-up
@@ -412,11 +413,14 @@ int qcldpc_autotune_shapes(const qcldpc_code *code, int n_frames, void *workspac
  * pass and then the variable-node pass of the decoder (with vn_pass = 0 the
  * light pass that turns the accumulated sums into posteriors) `reps` times
  * each, with
- * the launch configuration qcldpc_decode uses, on the state a previous
- * qcldpc_decode / qcldpc_decode_soft call with the same code, n_frames and
- * workspace left behind, and returns each pass's mean duration in
+ * the launch configuration qcldpc_decode uses for the whole batch, on the
+ * workspace of a previous qcldpc_decode / qcldpc_decode_soft call with the
+ * same code and n_frames, and returns each pass's mean duration in
  * milliseconds (CUDA events on `stream`). The replays run as iteration 2 of
  * a decode with every frame active, so each moves a full iteration's data.
+ * After a decode that ran its frames in groups (frame_groups), the replays
+ * read the workspace through the whole batch's layout: the same kernels,
+ * launch shapes and bytes, on values that are not that decode's state.
  * Overwrites the decoder state in the workspace (the last decode's outputs
  * are untouched). Blocks the calling thread until the replays finish.
  * Errors: QCLDPC_E_INVAL (no matching previous decode), _NOMEM, _CUDA.
