@@ -1161,14 +1161,15 @@ extern "C" int qcldpc_decode_soft(const qcldpc_code *code, const float *llr_dev,
 // ---------------------------------------------------------------------------
 // Batched decoding: the frames of several codes in one graph launch.
 //
-// The graph initialises every code's frames, then runs one device-side loop
-// (a conditional WHILE node) whose body holds, for every code, the same
-// chain of flooding passes a one-code decode runs (check pass, control step,
-// posterior pass, kLoopUnroll times), side by side, so the small grids of
-// short codes fill the GPU together; a last step of the body keeps the loop
-// running while any frame of any code is active. Each frame keeps its own
-// iteration counter and stop test, so its result is the one a one-code
-// decode of the same frames gives.
+// The graph holds, for every code (or every frame group of one code), the
+// chain a one-code decode runs: initialisation, a device-side loop (a
+// conditional WHILE node) over the flooding passes (check pass, control
+// step, posterior pass, kLoopUnroll times per trip) whose control steps end
+// it once the chain's own frames have stopped, and the output step. The
+// chains are independent branches, so the small grids of short codes fill
+// the GPU together and one chain's short steps run inside another's check
+// pass. Each frame keeps its own iteration counter and stop test, so its
+// result is the one a one-code decode of the same frames gives.
 namespace {
 
 constexpr int kMultiMaxCodes = QCLDPC_MULTI_MAX_CODES;
