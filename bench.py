@@ -224,6 +224,14 @@ def iteration_bytes(Z: int, n_h: int, n_d1: int, n_hcols: int, mb: int, msg_byte
             + (mb * Z + 2 * n_d1 * Z) / 8)
 
 
+def launch_count(group_passes, per_pass: int, unroll: int) -> int:
+    """Library kernels one decode step launches: the LLR map, an init and a
+    final kernel per frame group, and per_pass kernels for every pass of
+    each group's own loop, whose trips run `unroll` passes each (passes
+    after the group's frames stopped still launch)."""
+    return 1 + 2 * len(group_passes) + sum(-(-p // unroll) * unroll * per_pass for p in group_passes)
+
+
 def groups_of(args, F):
     """Frame groups the decode runs as (the library's rule for frame_groups:
     by default two for flooding, one chain for layered decoding)."""
@@ -485,8 +493,7 @@ def run_ours(args, world, rank, local):
         loop_passes = [args.max_iter + 1] * B
         group_passes = [[args.max_iter + 1] * G for _ in range(B)]
     unroll = 4 if (not layered and args.launch_mode != "stream") else 1
-    launches = sum(1 + 2 * G + sum(-(-p // unroll) * unroll * per_pass for p in group_passes[s % B])
-                   for s in range(args.steps))
+    launches = sum(launch_count(group_passes[s % B], per_pass, unroll) for s in range(args.steps))
 
     # --- end to end: pinned host inputs -> device -> keys/flags back to host.
     # Two staging buffers and a copy stream: the inputs of step s+1 are copied
