@@ -204,3 +204,25 @@ def test_frame_groups_rejects_out_of_range():
     with pytest.raises(q.QcldpcError, match="INVAL"):
         q.qcldpc_decode(code, x, s, 2, 10, q.qcldpc_params_init(frame_groups=17), dec.keys,
                         dec.converged, dec.iters, dec.workspace, dec.ws_bytes)
+
+
+def test_frame_groups_edge_iterations_and_graph_reuse():
+    """Grouped and one-chain decodes agree at max_iter 0 and 1 (the first
+    trip ends every group's loop), and a second decode of other frames
+    through the same cached grouped graph equals a fresh one-chain decode
+    (each group's state is re-initialised by its own init kernel)."""
+    d = synth.rate002_code(64)
+    code = q.create_code_from(d)
+    fa = make_frames(d, 0.05, 6, seed0=9840)
+    fb = make_frames(d, 0.06, 6, seed0=9860)
+    ia, ib = _inputs(fa), _inputs(fb)
+    grouped = q.Decoder(code, 6)  # default: two groups of 3
+    for max_iter in (0, 1, 30):
+        ref = q.Decoder(code, 6, q.qcldpc_params_init(frame_groups=1))
+        for inp in (ia, ib):
+            ref.decode(inp[0], inp[1], max_iter)
+            grouped.decode(inp[0], inp[1], max_iter)
+            torch.cuda.synchronize()
+            assert torch.equal(grouped.keys, ref.keys), max_iter
+            assert torch.equal(grouped.converged, ref.converged), max_iter
+            assert torch.equal(grouped.iters, ref.iters), max_iter
